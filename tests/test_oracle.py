@@ -385,3 +385,20 @@ def test_residual_replacement_matches_scipy_restart():
             assert out["status"][c] == oracle.CONVERGED
             assert out["iters"][c] == it1 + it2, (c, out["iters"][c], it1, it2)
     assert checked >= 1
+
+
+def test_initial_guess_iteration_counts_equal_scipy():
+    """With x0 given, r0 = b - A x0 and the shadow vector r^ = r0 (SciPy does
+    the same): counts and solutions agree."""
+    scipy_sparse = pytest.importorskip("scipy.sparse")
+    cbs, tol, maxit = synth.workload(1, cells=30)
+    cb = cbs[0]
+    m = cb.mech
+    x0 = np.random.default_rng(5).standard_normal((30, m.n))
+    out = oracle.solve(m.row_ptr, m.col_idx, cb.A_vals, cb.b, tol, maxit, x0=x0)
+    for c in range(30):
+        A = scipy_sparse.csr_matrix((cb.A_vals[c], m.col_idx, m.row_ptr), shape=(m.n, m.n))
+        it, xs, info = _scipy_count(A, cb.b[c], tol, maxit, x0=x0[c].copy())
+        assert info == 0
+        assert out["iters"][c] == it, (c, out["iters"][c], it)
+        np.testing.assert_allclose(out["x"][c], xs, rtol=1e-9, atol=1e-9 * np.abs(xs).max())
