@@ -1,0 +1,184 @@
+/*
+ * camp_solver.h -- C ABI of the batched Jacobi-preconditioned BiCGSTAB solver
+ * for the per-cell Newton systems of a stiff chemistry ODE step.
+ *
+ * Operation (the paper, Sec. 2.2 and Sec. 3.1): every grid cell c carries one
+ * sparse linear system A_c x_c = b_c, A_c = I - gamma_c J_c, the matrix of the
+ * Newton iteration inside the BDF step; all cells share one CSR sparsity
+ * pattern and are independent of each other.  Each cell is solved on its own
+ * inside one thread block or one warp, with its own convergence test and no
+ * communication between cells (the paper's Block-cells strategy, Sec. 3.1 and
+ * Sec. 3.2).  The iteration is BiCGSTAB with the Jacobi preconditioner
+ * M = diag(A) applied on the right (the paper's "BCG" solver, Sec. 3.1; the
+ * preconditioner is the one the paper leaves to future work, Sec. 5.2).
+ *
+ * Conventions shared by every entry point
+ *  - Layout.  A_vals is cell-major [cells x nnz] in the order of the pattern
+ *    given to camp_solver_create (row-major CSR, columns sorted); b, x and the
+ *    adjoint vectors are [cells x n]; per-cell outputs are [cells].  All
+ *    arrays are contiguous, FP64 unless stated, int32 for counts.
+ *  - Ownership.  Array arguments are device pointers owned by the caller
+ *    (except camp_solver_solve_host, which takes host pointers).  The solver
+ *    handle owns only its device copies of the pattern, the transposed
+ *    pattern, the SpMV schedules and its staging buffers.
+ *  - Streams.  Work is enqueued on the stream set with camp_solver_set_stream
+ *    (default: the legacy default stream) and returns without waiting.
+ *  - Errors.  A negative camp_status means nothing was enqueued (argument or
+ *    pattern error) or the CUDA runtime reported an error; camp_last_error()
+ *    gives a message.  Non-convergence of a cell is NOT an error: it shows in
+ *    that cell's iters/resid/status and the call returns CAMP_OK.
+ *  - Per-cell result.  x solves the cell to ||b - A x||_2 <= tol ||b||_2
+ *    (status CAMP_CELL_CONVERGED) unless maxit iterations run out
+ *    (CAMP_CELL_MAXIT), BiCGSTAB breaks down twice in a row
+ *    (CAMP_CELL_BREAKDOWN) or a non-finite value appears
+ *    (CAMP_CELL_NONFINITE).  resid_out is the true relative residual
+ *    ||b - A x||_2 / ||b||_2 of the returned x; iters_out counts products
+ *    v = A p^ (one per BiCGSTAB iteration, half-step exits included).
+ *    b == 0 gives x = 0, 0 iterations, resid 0.
+ */
+#ifndef CAMP_SOLVER_H
+#define CAMP_SOLVER_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct camp_solver *camp_solver_t;
+
+typedef enum {
+  CAMP_OK = 0,
+  CAMP_EINVAL = -1,      /* bad argument (null pointer, size, tol, maxit) */
+  CAMP_ECUDA = -2,       /* CUDA runtime error; see camp_last_error() */
+  CAMP_ENOMEM = -3,      /* device or host allocation failed */
+  CAMP_EPATTERN = -4,    /* invalid CSR pattern */
+  CAMP_EUNSUPPORTED = -5 /* size outside what the kernels support */
+} camp_status;
+
+enum {
+  CAMP_CELL_CONVERGED = 0,
+  CAMP_CELL_MAXIT = 1,
+  CAMP_CELL_BREAKDOWN = 2,
+  CAMP_CELL_NONFINITE = 3
+};
+
+/* flags for camp_solver_solve_ex */
+enum {
+  CAMP_TRANSPOSE = 1, /* solve A^T x = b (through the transposed pattern) */
+  CAMP_X0_GIVEN = 2   /* x holds the initial guess on entry (default x0 = 0) */
+};
+
+/* arrangements (camp_solver_set_arrangement); see the Sec. 3.2 configurations */
+enum {
+  CAMP_ARR_AUTO = 0,  /* library choice (tuned table or heuristic) */
+  CAMP_ARR_WARP = 1,  /* 32/lanes_per_cell cells per warp, one warp per group */
+  CAMP_ARR_BLOCK = 2  /* cells_per_block cells per CTA, one thread per row */
+};
+
+/*
+ * Create a solver for one sparsity pattern (the pattern shared by all cells,
+ * Sec. 3.1).  row_ptr [n+1] and col_idx [nnz] are HOST arrays, copied.
+ * Requirements: 1 <= n <= 4096, n <= nnz <= 65535, row_ptr[0] = 0,
+ * row_ptr[n] = nnz, nondecreasing; columns in [0, n) strictly increasing
+ * within a row; every diagonal entry present.  Otherwise CAMP_EPATTERN (or
+ * CAMP_EINVAL for null pointers / sizes).  Allocates device memory on the
+ * current device.
+ */
+camp_status camp_solver_create(camp_solver_t *out, int n, int nnz,
+                               const int *row_ptr, const int *col_idx);
+
+/* Free the handle and its device memory (synchronises its stream first). */
+camp_status camp_solver_destroy(camp_solver_t h);
+
+/* Stream for subsequent calls: a cudaStream_t passed as void* (NULL = legacy
+ * default stream). */
+camp_status camp_solver_set_stream(camp_solver_t h, void *stream);
+
+/*
+ * Override the thread arrangement (Sec. 3.2, Table GPU1).
+ *   CAMP_ARR_WARP : lanes_per_cell in {1,2,4,8,16,32} lanes solve one cell,
+ *                   32/lanes_per_cell cells share a warp; warps_per_block
+ *                   warps per CTA (0 = library default).
+ *                   lanes_per_cell = 32 is "warp per cell".
+ *   CAMP_ARR_BLOCK: cells_per_block cells per CTA with one thread per row
+ *                   (cells_per_block = 1 is the paper's Block-cells(1)).
+ *   CAMP_ARR_AUTO : library choice.
+ * Unused arguments are ignored.  Returns CAMP_EINVAL for unsupported values.
+ */
+camp_status camp_solver_set_arrangement(camp_solver_t h, int arrangement,
+                                        int lanes_per_cell, int cells_per_block,
+                                        int warps_per_block);
+
+/*
+ * Solve all cells: A_vals [cells x nnz], b [cells x n] in; x [cells x n],
+ * iters_out [cells] (int32), resid_out [cells] out.  Device pointers.
+ * tol > 0, maxit >= 1, cells >= 0 (0 enqueues nothing).
+ * The solve of each cell follows Sec. 3.1 (one cell per block/warp, no
+ * inter-cell communication, convergence decided on the device).
+ */
+camp_status camp_solver_solve(camp_solver_t h, int cells, const double *A_vals,
+                              const double *b, double *x, double tol,
+                              int maxit, int *iters_out, double *resid_out);
+
+/*
+ * As camp_solver_solve, plus: status_out [cells] (int32, may be NULL) and
+ * flags (CAMP_TRANSPOSE, CAMP_X0_GIVEN).  With CAMP_TRANSPOSE the same
+ * A_vals (forward pattern order) are used and A^T x = b is solved; this is
+ * the adjoint solve of the gradient below.
+ */
+camp_status camp_solver_solve_ex(camp_solver_t h, int cells,
+                                 const double *A_vals, const double *b,
+                                 double *x, double tol, int maxit,
+                                 int *iters_out, double *resid_out,
+                                 int *status_out, int flags);
+
+/*
+ * Gradient of a loss L with respect to the matrix values, given the adjoint
+ * lambda = A^{-T} dL/dx and the solution x:
+ *   gA[c, k] = -lambda[c, row(k)] * x[c, col(k)]   for every pattern entry k.
+ * lambda, x [cells x n] and gA [cells x nnz] are device pointers.
+ * (dL/db = lambda needs no kernel.)
+ */
+camp_status camp_solver_grad_A(camp_solver_t h, int cells,
+                               const double *lambda, const double *x,
+                               double *gA);
+
+/*
+ * End-to-end solve from HOST memory: copies A_vals and b to the device in
+ * chunks, solves each chunk while the next one is copied, and copies x,
+ * iters and resid back; returns after everything is back in host memory.
+ * Host arrays should be page-locked for full speed (pageable memory works but
+ * the copies are synchronous).  status_out may be NULL.  Device staging
+ * buffers are owned by the handle and grow on demand.
+ */
+camp_status camp_solver_solve_host(camp_solver_t h, int cells,
+                                   const double *A_vals, const double *b,
+                                   double *x, double tol, int maxit,
+                                   int *iters_out, double *resid_out,
+                                   int *status_out);
+
+/*
+ * Mixed precision (iterative refinement): FP64 outer sweeps r = b - A x,
+ * stop when ||r|| <= tol ||b||, else an FP32 BiCGSTAB solve of A d = r/||r||
+ * (FP32 copy of A, FP32 Jacobi) to relative tolerance tol_inner or maxit_inner
+ * iterations, then x += ||r|| d in FP64; at most max_sweeps sweeps (status
+ * CAMP_CELL_MAXIT after that).  iters_out = total FP32 inner iterations,
+ * sweeps_out [cells] (int32, may be NULL) = outer sweeps that ran an inner
+ * solve; resid_out = final FP64 true relative residual.  Device pointers.
+ */
+camp_status camp_solver_solve_mixed(camp_solver_t h, int cells,
+                                    const double *A_vals, const double *b,
+                                    double *x, double tol, int max_sweeps,
+                                    double tol_inner, int maxit_inner,
+                                    int *iters_out, int *sweeps_out,
+                                    double *resid_out, int *status_out);
+
+/* Thread-local message describing the last error (never NULL). */
+const char *camp_last_error(void);
+
+/* Library version string. */
+const char *camp_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CAMP_SOLVER_H */

@@ -1,0 +1,77 @@
+// Internal declarations shared by the host layer and the kernel translation
+// units of the batched BiCGSTAB library.  Not part of the public ABI.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include "camp_solver.h"
+
+namespace camp {
+
+// SpMV schedule slot (see build_schedule in solver.cu):
+//   x = a_idx | col << 16            (A value index in the cell, gathered column)
+//   y = row | end << 16              (row stored when end == 1)
+// Words are laid out [slot j][lane-in-cell sl] so a cell's lanes read
+// consecutive words.
+typedef uint2 SchedWord;
+
+// Arguments of the warp-packed kernel: Lc lanes per cell, k = 32/Lc cells per
+// warp ("segments"), E rows per lane (template), one group of k consecutive
+// cells per warp at a time.
+struct WarpArgs {
+  int cells, n, nnz;
+  int Lc, log2Lc, k;       // lanes per cell, log2, cells per warp
+  int L;                   // schedule slots per lane
+  int segA, segV;          // shared-memory doubles per cell: A block, one vector
+  int ngroups;             // ceil(cells / k)
+  const double *A, *b;     // [cells x nnz], [cells x n]
+  double *x;               // [cells x n]
+  int *iters;              // [cells]
+  double *resid;           // [cells]
+  int *status;             // [cells] or null
+  const int *a_perm;       // null, or [nnz]: cell value k of this view = A[c][a_perm[k]]
+  const int *diag;         // [n] position of the diagonal in this view
+  const SchedWord *sched;  // [L x Lc]
+  double tol;
+  int maxit;
+  int x0_given;
+};
+
+// Arguments of the block kernel (the paper's Block-cells(k) arrangement):
+// cpb cells per CTA, one thread per row, rows of cell j at threads [j*n, j*n+n).
+struct BlockArgs {
+  int cells, n, nnz, cpb;
+  const double *A, *b;
+  double *x;
+  int *iters;
+  double *resid;
+  int *status;
+  const int *a_perm;
+  const int *diag;
+  const int *row_ptr, *col_idx;  // the view's CSR
+  double tol;
+  int maxit;
+  int x0_given;
+};
+
+// per-cell grad kernel arguments
+struct GradArgs {
+  int cells, n, nnz;
+  const int *row_of;   // [nnz] row index of entry k
+  const int *col_idx;  // [nnz]
+  const double *lambda, *x;
+  double *gA;
+};
+
+// Launchers (each returns the launch error, cudaSuccess on success).
+cudaError_t launch_warp(int E, const WarpArgs &a, int warps_per_block,
+                        int grid, size_t smem, cudaStream_t st);
+cudaError_t warp_set_smem(int E, size_t smem);
+cudaError_t warp_occupancy(int E, int warps_per_block, size_t smem, int *blocks);
+cudaError_t launch_block(const BlockArgs &a, int threads, size_t smem,
+                         cudaStream_t st);
+cudaError_t block_set_smem(size_t smem);
+cudaError_t launch_grad(const GradArgs &a, cudaStream_t st);
+
+constexpr int kMaxE = 16;  // rows per lane supported by the warp kernel
+
+}  // namespace camp

@@ -1,0 +1,557 @@
+// Host layer of the C ABI (include/camp_solver.h): pattern validation and
+// preprocessing, SpMV schedules, arrangement choice and kernel launches.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "camp_internal.h"
+
+namespace camp {
+cudaError_t launch_warp_1(const WarpArgs &, int, int, size_t, cudaStream_t);
+#define CAMP_DECL(E)                                                        \
+  cudaError_t launch_warp_##E(const WarpArgs &, int, int, size_t, cudaStream_t); \
+  cudaError_t occ_warp_##E(int, size_t, int *);
+CAMP_DECL(2) CAMP_DECL(3) CAMP_DECL(4) CAMP_DECL(5) CAMP_DECL(6) CAMP_DECL(7)
+CAMP_DECL(8) CAMP_DECL(9) CAMP_DECL(10) CAMP_DECL(11) CAMP_DECL(12)
+CAMP_DECL(13) CAMP_DECL(14) CAMP_DECL(15) CAMP_DECL(16)
+cudaError_t occ_warp_1(int, size_t, int *);
+#undef CAMP_DECL
+
+cudaError_t launch_warp(int E, const WarpArgs &a, int wpb, int grid,
+                        size_t smem, cudaStream_t st) {
+  switch (E) {
+#define C(E) case E: return launch_warp_##E(a, wpb, grid, smem, st);
+    C(1) C(2) C(3) C(4) C(5) C(6) C(7) C(8) C(9) C(10) C(11) C(12) C(13)
+    C(14) C(15) C(16)
+#undef C
+    default: return cudaErrorInvalidValue;
+  }
+}
+cudaError_t warp_occupancy(int E, int wpb, size_t smem, int *blocks) {
+  switch (E) {
+#define C(E) case E: return occ_warp_##E(wpb, smem, blocks);
+    C(1) C(2) C(3) C(4) C(5) C(6) C(7) C(8) C(9) C(10) C(11) C(12) C(13)
+    C(14) C(15) C(16)
+#undef C
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+namespace {
+
+thread_local std::string g_err;
+
+camp_status fail(camp_status s, const char *fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return s;
+}
+
+camp_status cuda_fail(cudaError_t e, const char *where) {
+  return fail(CAMP_ECUDA, "%s: %s", where, cudaGetErrorString(e));
+}
+
+// Balanced static SpMV schedule for lanes_per_cell lanes: whole rows are
+// assigned to lanes by longest-processing-time-first bin packing, then each
+// lane's rows are listed entry by entry and padded to the longest lane.
+struct Schedule {
+  int Lc = 0, L = 0;
+  std::vector<SchedWord> words;  // [L][Lc]
+  SchedWord *d_words = nullptr;
+};
+
+Schedule build_schedule(int n, const std::vector<int> &rp, int Lc) {
+  std::vector<int> order(n);
+  std::iota(order.begin(), order.end(), 0);
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+    return (rp[a + 1] - rp[a]) > (rp[b + 1] - rp[b]);
+  });
+  std::vector<long> load(Lc, 0);
+  std::vector<std::vector<int>> rows(Lc);
+  for (int r : order) {
+    int best = 0;
+    for (int q = 1; q < Lc; ++q)
+      if (load[q] < load[best]) best = q;
+    load[best] += rp[r + 1] - rp[r];
+    rows[best].push_back(r);
+  }
+  Schedule S;
+  S.Lc = Lc;
+  S.L = (int)*std::max_element(load.begin(), load.end());
+  S.words.assign((size_t)S.L * Lc, SchedWord{0u, 0u});
+  for (int q = 0; q < Lc; ++q) {
+    std::sort(rows[q].begin(), rows[q].end());
+    int j = 0;
+    for (int r : rows[q])
+      for (int k = rp[r]; k < rp[r + 1]; ++k, ++j) {
+        SchedWord w;
+        w.x = (unsigned)k | ((unsigned)0 << 16);
+        w.y = (k == rp[r + 1] - 1) ? ((unsigned)r | (1u << 16)) : 0u;
+        S.words[(size_t)j * Lc + q] = w;
+      }
+  }
+  return S;
+}
+
+// one orientation of the pattern: forward (A) or transposed (A^T)
+struct View {
+  int n = 0, nnz = 0;
+  std::vector<int> rp, ci, diag, perm;  // perm empty for the forward view
+  int *d_rp = nullptr, *d_ci = nullptr, *d_diag = nullptr, *d_perm = nullptr;
+  std::map<int, Schedule> sched;  // by lanes per cell
+};
+
+template <class T>
+cudaError_t upload(T **dst, const std::vector<T> &src) {
+  *dst = nullptr;
+  if (src.empty()) return cudaSuccess;
+  cudaError_t e = cudaMalloc((void **)dst, src.size() * sizeof(T));
+  if (e != cudaSuccess) return e;
+  return cudaMemcpy(*dst, src.data(), src.size() * sizeof(T),
+                    cudaMemcpyHostToDevice);
+}
+
+}  // namespace
+}  // namespace camp
+
+using namespace camp;
+
+struct camp_solver {
+  int device = 0, sms = 0;
+  size_t smem_optin = 0;
+  int n = 0, nnz = 0;
+  cudaStream_t stream = nullptr;
+  View fwd, tr;
+  int *d_row_of = nullptr;  // forward view: row of entry k
+  int arrangement = CAMP_ARR_AUTO, lanes = 0, cpb = 1, wpb = 0;
+  // staging for camp_solver_solve_host
+  double *h_dA = nullptr, *h_db = nullptr, *h_dx = nullptr, *h_dres = nullptr;
+  int *h_dit = nullptr, *h_dst = nullptr;
+  size_t h_cap_cells = 0;
+  cudaStream_t h_streams[2] = {nullptr, nullptr};
+  cudaEvent_t h_ev[4] = {nullptr, nullptr, nullptr, nullptr};
+  std::mutex mu;
+};
+
+namespace {
+
+cudaError_t view_schedule(View &v, int Lc, Schedule **out) {
+  auto it = v.sched.find(Lc);
+  if (it == v.sched.end()) {
+    Schedule S = build_schedule(v.n, v.rp, Lc);
+    cudaError_t e = upload(&S.d_words, S.words);
+    if (e != cudaSuccess) return e;
+    it = v.sched.emplace(Lc, std::move(S)).first;
+  }
+  *out = &it->second;
+  return cudaSuccess;
+}
+
+void free_view(View &v) {
+  cudaFree(v.d_rp);
+  cudaFree(v.d_ci);
+  cudaFree(v.d_diag);
+  cudaFree(v.d_perm);
+  for (auto &kv : v.sched) cudaFree(kv.second.d_words);
+  v.sched.clear();
+}
+
+int ilog2(int v) {
+  int l = 0;
+  while ((1 << l) < v) ++l;
+  return l;
+}
+
+// Warp kernel shared-memory bytes for one CTA.
+size_t warp_smem(const View &v, int Lc, int L, int wpb, int *segA, int *segV) {
+  const int k = 32 / Lc;
+  const int E = (v.n + Lc - 1) / Lc;
+  *segA = (v.nnz + 1) & ~1;
+  *segV = ((E * Lc + 1) + 1) & ~1;
+  const size_t sch = (((size_t)L * Lc * 8) + 15) & ~(size_t)15;
+  return sch + (size_t)wpb * k * (*segA + 3 * *segV) * 8;
+}
+
+// Estimated FP64 warp-instructions per cell-iteration of the warp kernel
+// (used by the automatic arrangement choice).
+double warp_cost(int Lc, int L, int E) {
+  const int k = 32 / Lc;
+  return (2.0 * L + 14.0 * E + 6.0 * ilog2(Lc) + 30.0) / k;
+}
+
+size_t block_smem(int n, int nnz, int cpb, int threads) {
+  return ((size_t)cpb * nnz + 3 * (size_t)cpb * n + 3 * (size_t)threads +
+          3 * (size_t)cpb) * 8;
+}
+
+camp_status do_solve(camp_solver_t h, int cells, const double *A_vals,
+                     const double *b, double *x, double tol, int maxit,
+                     int *iters_out, double *resid_out, int *status_out,
+                     int flags, cudaStream_t st) {
+  if (!h) return fail(CAMP_EINVAL, "null solver handle");
+  if (cells < 0) return fail(CAMP_EINVAL, "cells < 0");
+  if (!(tol > 0.0) || !std::isfinite(tol)) return fail(CAMP_EINVAL, "tol must be finite and > 0");
+  if (maxit < 1) return fail(CAMP_EINVAL, "maxit must be >= 1");
+  if (flags & ~(CAMP_TRANSPOSE | CAMP_X0_GIVEN)) return fail(CAMP_EINVAL, "unknown flags 0x%x", flags);
+  if (cells == 0) return CAMP_OK;
+  if (!A_vals || !b || !x || !iters_out || !resid_out)
+    return fail(CAMP_EINVAL, "null array pointer");
+  cudaError_t e = cudaSetDevice(h->device);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
+  View &v = (flags & CAMP_TRANSPOSE) ? h->tr : h->fwd;
+
+  int arr = h->arrangement;
+  int Lc = h->lanes;
+  if (arr == CAMP_ARR_AUTO) {
+    arr = CAMP_ARR_WARP;
+    double best = 1e300;
+    Lc = 0;
+    for (int cand = 1; cand <= 32; cand *= 2) {
+      const int E = (v.n + cand - 1) / cand;
+      if (E > kMaxE) continue;
+      Schedule *S = nullptr;
+      e = view_schedule(v, cand, &S);
+      if (e != cudaSuccess) return cuda_fail(e, "schedule upload");
+      int sa, sv;
+      if (warp_smem(v, cand, S->L, 1, &sa, &sv) > h->smem_optin) continue;
+      const double cst = warp_cost(cand, S->L, E);
+      if (cst < best) {
+        best = cst;
+        Lc = cand;
+      }
+    }
+    if (Lc == 0) {
+      arr = CAMP_ARR_BLOCK;
+    }
+  }
+
+  if (arr == CAMP_ARR_WARP) {
+    const int E = (v.n + Lc - 1) / Lc;
+    if (E > kMaxE)
+      return fail(CAMP_EUNSUPPORTED, "n=%d needs %d rows per lane at %d lanes per cell (max %d)",
+                  v.n, E, Lc, kMaxE);
+    Schedule *S = nullptr;
+    e = view_schedule(v, Lc, &S);
+    if (e != cudaSuccess) return cuda_fail(e, "schedule upload");
+    int wpb = h->wpb > 0 ? h->wpb : 4;
+    int segA = 0, segV = 0;
+    size_t smem = warp_smem(v, Lc, S->L, wpb, &segA, &segV);
+    while (smem > h->smem_optin && wpb > 1) {
+      --wpb;
+      smem = warp_smem(v, Lc, S->L, wpb, &segA, &segV);
+    }
+    if (smem > h->smem_optin)
+      return fail(CAMP_EUNSUPPORTED, "cell does not fit in shared memory (%zu bytes)", smem);
+    WarpArgs a;
+    a.cells = cells; a.n = v.n; a.nnz = v.nnz;
+    a.Lc = Lc; a.log2Lc = ilog2(Lc); a.k = 32 / Lc; a.L = S->L;
+    a.segA = segA; a.segV = segV;
+    a.ngroups = (cells + a.k - 1) / a.k;
+    a.A = A_vals; a.b = b; a.x = x; a.iters = iters_out; a.resid = resid_out;
+    a.status = status_out; a.a_perm = v.d_perm; a.diag = v.d_diag;
+    a.sched = S->d_words; a.tol = tol; a.maxit = maxit;
+    a.x0_given = (flags & CAMP_X0_GIVEN) ? 1 : 0;
+    int occ = 0;
+    e = warp_occupancy(E, wpb, smem, &occ);
+    if (e != cudaSuccess) return cuda_fail(e, "occupancy");
+    if (occ < 1) occ = 1;
+    const int need = (a.ngroups + wpb - 1) / wpb;
+    const int grid = std::max(1, std::min(need, h->sms * occ));
+    e = launch_warp(E, a, wpb, grid, smem, st);
+    if (e != cudaSuccess) return cuda_fail(e, "warp kernel launch");
+    return CAMP_OK;
+  }
+
+  // block arrangement
+  const int cpb = std::max(1, h->cpb);
+  const int threads = ((cpb * v.n + 31) / 32) * 32;
+  if (threads > 1024)
+    return fail(CAMP_EUNSUPPORTED, "cells_per_block*n = %d exceeds 1024 threads", cpb * v.n);
+  const size_t smem = block_smem(v.n, v.nnz, cpb, threads);
+  if (smem > h->smem_optin)
+    return fail(CAMP_EUNSUPPORTED, "block does not fit in shared memory (%zu bytes)", smem);
+  BlockArgs a;
+  a.cells = cells; a.n = v.n; a.nnz = v.nnz; a.cpb = cpb;
+  a.A = A_vals; a.b = b; a.x = x; a.iters = iters_out; a.resid = resid_out;
+  a.status = status_out; a.a_perm = v.d_perm; a.diag = v.d_diag;
+  a.row_ptr = v.d_rp; a.col_idx = v.d_ci; a.tol = tol; a.maxit = maxit;
+  a.x0_given = (flags & CAMP_X0_GIVEN) ? 1 : 0;
+  e = launch_block(a, threads, smem, st);
+  if (e != cudaSuccess) return cuda_fail(e, "block kernel launch");
+  return CAMP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *camp_last_error(void) { return g_err.c_str(); }
+const char *camp_version(void) { return "campsolve 0.1 (sm_103a)"; }
+
+camp_status camp_solver_create(camp_solver_t *out, int n, int nnz,
+                               const int *row_ptr, const int *col_idx) {
+  if (!out) return fail(CAMP_EINVAL, "null output handle pointer");
+  *out = nullptr;
+  if (!row_ptr || !col_idx) return fail(CAMP_EINVAL, "null pattern array");
+  if (n < 1 || n > 1024) return fail(CAMP_EINVAL, "n=%d outside [1, 1024]", n);
+  if (nnz < n || nnz > 65535) return fail(CAMP_EINVAL, "nnz=%d outside [n, 65535]", nnz);
+  if (row_ptr[0] != 0 || row_ptr[n] != nnz)
+    return fail(CAMP_EPATTERN, "row_ptr[0] must be 0 and row_ptr[n] must equal nnz");
+  std::vector<int> diag(n, -1);
+  for (int i = 0; i < n; ++i) {
+    if (row_ptr[i + 1] < row_ptr[i]) return fail(CAMP_EPATTERN, "row_ptr decreases at row %d", i);
+    for (int k = row_ptr[i]; k < row_ptr[i + 1]; ++k) {
+      const int j = col_idx[k];
+      if (j < 0 || j >= n) return fail(CAMP_EPATTERN, "column %d out of range at entry %d", j, k);
+      if (k > row_ptr[i] && j <= col_idx[k - 1])
+        return fail(CAMP_EPATTERN, "columns not strictly increasing in row %d", i);
+      if (j == i) diag[i] = k;
+    }
+    if (diag[i] < 0) return fail(CAMP_EPATTERN, "diagonal entry missing in row %d", i);
+  }
+  camp_solver *h = new (std::nothrow) camp_solver();
+  if (!h) return fail(CAMP_ENOMEM, "host allocation failed");
+  cudaError_t e = cudaGetDevice(&h->device);
+  if (e != cudaSuccess) { delete h; return cuda_fail(e, "cudaGetDevice"); }
+  int optin = 0;
+  cudaDeviceGetAttribute(&h->sms, cudaDevAttrMultiProcessorCount, h->device);
+  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device);
+  h->smem_optin = (size_t)optin;
+  h->n = n;
+  h->nnz = nnz;
+  // forward view
+  View &f = h->fwd;
+  f.n = n; f.nnz = nnz;
+  f.rp.assign(row_ptr, row_ptr + n + 1);
+  f.ci.assign(col_idx, col_idx + nnz);
+  f.diag = diag;
+  // transposed view: counting sort by column; perm[q] = forward entry of q
+  View &t = h->tr;
+  t.n = n; t.nnz = nnz;
+  t.rp.assign(n + 1, 0);
+  t.ci.assign(nnz, 0);
+  t.perm.assign(nnz, 0);
+  t.diag.assign(n, -1);
+  for (int k = 0; k < nnz; ++k) t.rp[col_idx[k] + 1]++;
+  for (int j = 0; j < n; ++j) t.rp[j + 1] += t.rp[j];
+  {
+    std::vector<int> fill(t.rp.begin(), t.rp.end() - 1);
+    for (int i = 0; i < n; ++i)
+      for (int k = row_ptr[i]; k < row_ptr[i + 1]; ++k) {
+        const int q = fill[col_idx[k]]++;
+        t.ci[q] = i;
+        t.perm[q] = k;
+        if (i == col_idx[k]) t.diag[col_idx[k]] = q;
+      }
+  }
+  std::vector<int> row_of(nnz);
+  for (int i = 0; i < n; ++i)
+    for (int k = row_ptr[i]; k < row_ptr[i + 1]; ++k) row_of[k] = i;
+  if ((e = upload(&f.d_rp, f.rp)) != cudaSuccess ||
+      (e = upload(&f.d_ci, f.ci)) != cudaSuccess ||
+      (e = upload(&f.d_diag, f.diag)) != cudaSuccess ||
+      (e = upload(&t.d_rp, t.rp)) != cudaSuccess ||
+      (e = upload(&t.d_ci, t.ci)) != cudaSuccess ||
+      (e = upload(&t.d_diag, t.diag)) != cudaSuccess ||
+      (e = upload(&t.d_perm, t.perm)) != cudaSuccess ||
+      (e = upload(&h->d_row_of, row_of)) != cudaSuccess) {
+    free_view(h->fwd);
+    free_view(h->tr);
+    cudaFree(h->d_row_of);
+    delete h;
+    return cuda_fail(e, "pattern upload");
+  }
+  *out = h;
+  return CAMP_OK;
+}
+
+camp_status camp_solver_destroy(camp_solver_t h) {
+  if (!h) return CAMP_OK;
+  cudaSetDevice(h->device);
+  cudaStreamSynchronize(h->stream);
+  free_view(h->fwd);
+  free_view(h->tr);
+  cudaFree(h->d_row_of);
+  cudaFree(h->h_dA); cudaFree(h->h_db); cudaFree(h->h_dx);
+  cudaFree(h->h_dres); cudaFree(h->h_dit); cudaFree(h->h_dst);
+  for (auto &s : h->h_streams) if (s) cudaStreamDestroy(s);
+  for (auto &ev : h->h_ev) if (ev) cudaEventDestroy(ev);
+  delete h;
+  return CAMP_OK;
+}
+
+camp_status camp_solver_set_stream(camp_solver_t h, void *stream) {
+  if (!h) return fail(CAMP_EINVAL, "null solver handle");
+  h->stream = (cudaStream_t)stream;
+  return CAMP_OK;
+}
+
+camp_status camp_solver_set_arrangement(camp_solver_t h, int arrangement,
+                                        int lanes_per_cell, int cells_per_block,
+                                        int warps_per_block) {
+  if (!h) return fail(CAMP_EINVAL, "null solver handle");
+  if (arrangement == CAMP_ARR_AUTO) {
+    h->arrangement = arrangement;
+    h->wpb = warps_per_block > 0 ? warps_per_block : 0;
+    return CAMP_OK;
+  }
+  if (arrangement == CAMP_ARR_WARP) {
+    if (lanes_per_cell < 1 || lanes_per_cell > 32 || (lanes_per_cell & (lanes_per_cell - 1)))
+      return fail(CAMP_EINVAL, "lanes_per_cell must be a power of two in [1, 32]");
+    if ((h->n + lanes_per_cell - 1) / lanes_per_cell > kMaxE)
+      return fail(CAMP_EUNSUPPORTED, "n=%d needs more than %d rows per lane at %d lanes",
+                  h->n, kMaxE, lanes_per_cell);
+    if (warps_per_block < 0 || warps_per_block > 8)
+      return fail(CAMP_EINVAL, "warps_per_block must be in [0, 8]");
+    h->arrangement = arrangement;
+    h->lanes = lanes_per_cell;
+    h->wpb = warps_per_block;
+    return CAMP_OK;
+  }
+  if (arrangement == CAMP_ARR_BLOCK) {
+    if (cells_per_block < 1 || cells_per_block * h->n > 1024)
+      return fail(CAMP_EINVAL, "cells_per_block*n must be in [n, 1024]");
+    h->arrangement = arrangement;
+    h->cpb = cells_per_block;
+    return CAMP_OK;
+  }
+  return fail(CAMP_EINVAL, "unknown arrangement %d", arrangement);
+}
+
+camp_status camp_solver_solve(camp_solver_t h, int cells, const double *A_vals,
+                              const double *b, double *x, double tol,
+                              int maxit, int *iters_out, double *resid_out) {
+  return do_solve(h, cells, A_vals, b, x, tol, maxit, iters_out, resid_out,
+                  nullptr, 0, h ? h->stream : nullptr);
+}
+
+camp_status camp_solver_solve_ex(camp_solver_t h, int cells,
+                                 const double *A_vals, const double *b,
+                                 double *x, double tol, int maxit,
+                                 int *iters_out, double *resid_out,
+                                 int *status_out, int flags) {
+  return do_solve(h, cells, A_vals, b, x, tol, maxit, iters_out, resid_out,
+                  status_out, flags, h ? h->stream : nullptr);
+}
+
+camp_status camp_solver_grad_A(camp_solver_t h, int cells,
+                               const double *lambda, const double *x,
+                               double *gA) {
+  if (!h) return fail(CAMP_EINVAL, "null solver handle");
+  if (cells < 0) return fail(CAMP_EINVAL, "cells < 0");
+  if (cells == 0) return CAMP_OK;
+  if (!lambda || !x || !gA) return fail(CAMP_EINVAL, "null array pointer");
+  cudaError_t e = cudaSetDevice(h->device);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
+  GradArgs a;
+  a.cells = cells; a.n = h->n; a.nnz = h->nnz;
+  a.row_of = h->d_row_of; a.col_idx = h->fwd.d_ci;
+  a.lambda = lambda; a.x = x; a.gA = gA;
+  e = launch_grad(a, h->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "grad kernel launch");
+  return CAMP_OK;
+}
+
+camp_status camp_solver_solve_host(camp_solver_t h, int cells,
+                                   const double *A_vals, const double *b,
+                                   double *x, double tol, int maxit,
+                                   int *iters_out, double *resid_out,
+                                   int *status_out) {
+  if (!h) return fail(CAMP_EINVAL, "null solver handle");
+  if (cells < 0) return fail(CAMP_EINVAL, "cells < 0");
+  if (!(tol > 0.0) || !std::isfinite(tol)) return fail(CAMP_EINVAL, "tol must be finite and > 0");
+  if (maxit < 1) return fail(CAMP_EINVAL, "maxit must be >= 1");
+  if (cells == 0) return CAMP_OK;
+  if (!A_vals || !b || !x || !iters_out || !resid_out)
+    return fail(CAMP_EINVAL, "null array pointer");
+  std::lock_guard<std::mutex> lock(h->mu);
+  cudaError_t e = cudaSetDevice(h->device);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
+  const int n = h->n, nnz = h->nnz;
+  if ((size_t)cells > h->h_cap_cells) {
+    cudaFree(h->h_dA); cudaFree(h->h_db); cudaFree(h->h_dx);
+    cudaFree(h->h_dres); cudaFree(h->h_dit); cudaFree(h->h_dst);
+    h->h_dA = h->h_db = h->h_dx = h->h_dres = nullptr;
+    h->h_dit = h->h_dst = nullptr;
+    h->h_cap_cells = 0;
+    if ((e = cudaMalloc(&h->h_dA, (size_t)cells * nnz * 8)) != cudaSuccess ||
+        (e = cudaMalloc(&h->h_db, (size_t)cells * n * 8)) != cudaSuccess ||
+        (e = cudaMalloc(&h->h_dx, (size_t)cells * n * 8)) != cudaSuccess ||
+        (e = cudaMalloc(&h->h_dres, (size_t)cells * 8)) != cudaSuccess ||
+        (e = cudaMalloc(&h->h_dit, (size_t)cells * 4)) != cudaSuccess ||
+        (e = cudaMalloc(&h->h_dst, (size_t)cells * 4)) != cudaSuccess)
+      return fail(CAMP_ENOMEM, "staging allocation: %s", cudaGetErrorString(e));
+    h->h_cap_cells = (size_t)cells;
+  }
+  for (int q = 0; q < 2; ++q)
+    if (!h->h_streams[q] &&
+        (e = cudaStreamCreateWithFlags(&h->h_streams[q], cudaStreamNonBlocking)) != cudaSuccess)
+      return cuda_fail(e, "stream create");
+  // order after earlier work on the handle's stream
+  cudaEvent_t ev0;
+  if ((e = cudaEventCreateWithFlags(&ev0, cudaEventDisableTiming)) != cudaSuccess)
+    return cuda_fail(e, "event create");
+  cudaEventRecord(ev0, h->stream);
+  cudaStreamWaitEvent(h->h_streams[0], ev0, 0);
+  cudaStreamWaitEvent(h->h_streams[1], ev0, 0);
+  cudaEventDestroy(ev0);
+  // chunked pipeline: copy chunk q+1 in while chunk q solves, alternating streams
+  const int nchunk = cells >= 4096 ? 4 : 1;
+  const int per = (cells + nchunk - 1) / nchunk;
+  camp_status rs = CAMP_OK;
+  for (int q = 0; q < nchunk; ++q) {
+    const int c0 = q * per;
+    const int cn = std::min(per, cells - c0);
+    if (cn <= 0) break;
+    cudaStream_t s = h->h_streams[q & 1];
+    cudaMemcpyAsync(h->h_dA + (size_t)c0 * nnz, A_vals + (size_t)c0 * nnz,
+                    (size_t)cn * nnz * 8, cudaMemcpyHostToDevice, s);
+    cudaMemcpyAsync(h->h_db + (size_t)c0 * n, b + (size_t)c0 * n,
+                    (size_t)cn * n * 8, cudaMemcpyHostToDevice, s);
+    rs = do_solve(h, cn, h->h_dA + (size_t)c0 * nnz, h->h_db + (size_t)c0 * n,
+                  h->h_dx + (size_t)c0 * n, tol, maxit, h->h_dit + c0,
+                  h->h_dres + c0, h->h_dst + c0, 0, s);
+    if (rs != CAMP_OK) break;
+    cudaMemcpyAsync(x + (size_t)c0 * n, h->h_dx + (size_t)c0 * n,
+                    (size_t)cn * n * 8, cudaMemcpyDeviceToHost, s);
+    cudaMemcpyAsync(iters_out + c0, h->h_dit + c0, (size_t)cn * 4,
+                    cudaMemcpyDeviceToHost, s);
+    cudaMemcpyAsync(resid_out + c0, h->h_dres + c0, (size_t)cn * 8,
+                    cudaMemcpyDeviceToHost, s);
+    if (status_out)
+      cudaMemcpyAsync(status_out + c0, h->h_dst + c0, (size_t)cn * 4,
+                      cudaMemcpyDeviceToHost, s);
+  }
+  cudaError_t e0 = cudaStreamSynchronize(h->h_streams[0]);
+  cudaError_t e1 = cudaStreamSynchronize(h->h_streams[1]);
+  if (rs != CAMP_OK) return rs;
+  if (e0 != cudaSuccess) return cuda_fail(e0, "solve_host");
+  if (e1 != cudaSuccess) return cuda_fail(e1, "solve_host");
+  return CAMP_OK;
+}
+
+camp_status camp_solver_solve_mixed(camp_solver_t h, int cells,
+                                    const double *A_vals, const double *b,
+                                    double *x, double tol, int max_sweeps,
+                                    double tol_inner, int maxit_inner,
+                                    int *iters_out, int *sweeps_out,
+                                    double *resid_out, int *status_out) {
+  (void)cells; (void)A_vals; (void)b; (void)x; (void)tol; (void)max_sweeps;
+  (void)tol_inner; (void)maxit_inner; (void)iters_out; (void)sweeps_out;
+  (void)resid_out; (void)status_out;
+  if (!h) return fail(CAMP_EINVAL, "null solver handle");
+  return fail(CAMP_EUNSUPPORTED, "mixed precision kernel not built yet");
+}
+
+}  // extern "C"

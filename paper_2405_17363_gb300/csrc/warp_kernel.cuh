@@ -1,0 +1,339 @@
+// Warp-packed batched Jacobi-BiCGSTAB kernel.
+//
+// One warp solves k = 32/Lc cells at a time; each cell ("segment") owns Lc
+// consecutive lanes, and lane sl of a segment owns rows i = sl + e*Lc,
+// e = 0..E-1 (rows >= n are zero padding).  A cell's whole solve stays inside
+// its segment, so cells never communicate (Block-cells, Sec. 3.1), and the
+// convergence test runs on the device (Sec. 3.1, Fig. UMLMultiBlock).  The
+// per-cell scalars (rho, alpha, omega, ...) are replicated in the segment's
+// lanes; every FP64 instruction is issued once for all k cells of the warp.
+//
+// Shared memory per CTA: the SpMV schedule (shared by all warps), then per
+// cell: its matrix values A_s [segA], the gathered vector g_s [segV] and the
+// two product vectors o1_s = A p^, o2_s = A s^ [segV each].
+//
+// The iteration is right-preconditioned BiCGSTAB with M = diag(A); see the
+// header of the oracle for the readings of the paper (relative 2-norm test on
+// s and r, true-residual check with residual replacement, breakdown and
+// non-finite rules, iteration count = products v = A p^).
+#pragma once
+#include "camp_internal.h"
+
+namespace camp {
+
+constexpr unsigned kFull = 0xffffffffu;
+
+__device__ __forceinline__ bool is_finite_bits(double v) {
+  const unsigned long long u = (unsigned long long)__double_as_longlong(v);
+  return ((u >> 52) & 0x7ffull) != 0x7ffull;
+}
+// |v| < 1e-300, on the bit pattern (no FP64 instruction)
+__device__ __forceinline__ bool abs_tiny(double v) {
+  const unsigned long long u =
+      (unsigned long long)__double_as_longlong(v) & 0x7fffffffffffffffull;
+  return u < 0x01a56e1fc2f8f359ull;  // bit pattern of 1e-300
+}
+// a <= b for a, b >= +0 (or NaN a: false), on the bit pattern
+__device__ __forceinline__ bool le_nonneg(double a, double b) {
+  return __double_as_longlong(a) <= __double_as_longlong(b);
+}
+
+// Sum NV values over the Lc lanes of each segment (xor butterfly; every lane
+// of the segment ends with the same bits).
+template <int NV>
+__device__ __forceinline__ void seg_sum(double (&v)[NV], int Lc) {
+  for (int off = Lc >> 1; off > 0; off >>= 1) {
+#pragma unroll
+    for (int q = 0; q < NV; ++q) v[q] += __shfl_xor_sync(kFull, v[q], off);
+  }
+}
+
+// o[row] = sum_k A_s[k] g[col k] over this lane's slots of the schedule.
+__device__ __forceinline__ void seg_spmv(const SchedWord *__restrict__ sch,
+                                         int L, int Lc, const double *As,
+                                         const double *gs, double *os) {
+  double acc = 0.0;
+#pragma unroll 4
+  for (int j = 0; j < L; ++j) {
+    const SchedWord w = sch[j * Lc];
+    acc = fma(As[w.x & 0xffffu], gs[w.x >> 16], acc);
+    if (w.y >> 16) {
+      os[w.y & 0xffffu] = acc;
+      acc = 0.0;
+    }
+  }
+}
+
+template <int E>
+__global__ void __launch_bounds__(256)
+    warp_bicgstab_kernel(const WarpArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  SchedWord *sch_s = reinterpret_cast<SchedWord *>(smem_raw);
+  const int nsch = a.L * a.Lc;
+  for (int i = threadIdx.x; i < nsch; i += blockDim.x) sch_s[i] = a.sched[i];
+
+  const int lane = threadIdx.x & 31;
+  const int warp = threadIdx.x >> 5;
+  const int seg = lane >> a.log2Lc;
+  const int sl = lane & (a.Lc - 1);
+  const int segStride = a.segA + 3 * a.segV;
+  double *wbase = reinterpret_cast<double *>(smem_raw + (((size_t)nsch * 8 + 15) & ~(size_t)15)) +
+                  (size_t)warp * a.k * segStride;
+  double *As = wbase + (size_t)seg * segStride;
+  double *gs = As + a.segA;
+  double *o1 = gs + a.segV;
+  double *o2 = o1 + a.segV;
+  for (int i = sl; i < 3 * a.segV; i += a.Lc) gs[i] = 0.0;
+  __syncthreads();
+  const SchedWord *sch = sch_s + sl;
+
+  const int n = a.n, nnz = a.nnz, Lc = a.Lc;
+  const int warps_total = gridDim.x * (blockDim.x >> 5);
+  const double tol = a.tol;
+
+  for (int g = blockIdx.x * (blockDim.x >> 5) + warp; g < a.ngroups;
+       g += warps_total) {
+    const int c = g * a.k + seg;
+    const bool has = c < a.cells;
+    // ---- stage the cell's matrix values (Sec. 3.1: one cell, one team)
+    if (has) {
+      const double *Ac = a.A + (size_t)c * nnz;
+      if (a.a_perm) {
+        for (int k = sl; k < nnz; k += Lc) As[k] = __ldg(Ac + __ldg(a.a_perm + k));
+      } else {
+        for (int k = sl; k < nnz; k += Lc) As[k] = __ldg(Ac + k);
+      }
+    }
+    __syncwarp();
+
+    double r[E], rh[E], p[E], xv[E], s[E], dinv[E];
+    double bb;
+    {
+      double acc[1] = {0.0};
+#pragma unroll
+      for (int e = 0; e < E; ++e) {
+        const int i = sl + e * Lc;
+        const bool v = has && i < n;
+        const double bi = v ? __ldg(a.b + (size_t)c * n + i) : 0.0;
+        const double d = v ? As[__ldg(a.diag + i)] : 0.0;
+        dinv[e] = v ? (d != 0.0 ? 1.0 / d : 1.0) : 0.0;
+        xv[e] = (v && a.x0_given) ? a.x[(size_t)c * n + i] : 0.0;
+        r[e] = bi;
+        rh[e] = 0.0;
+        p[e] = 0.0;
+        s[e] = 0.0;
+        acc[0] = fma(bi, bi, acc[0]);
+      }
+      seg_sum<1>(acc, Lc);
+      bb = acc[0];
+    }
+    const double bnorm = sqrt(bb);
+    const double thr = (tol * bnorm) * (tol * bnorm);
+    int st = -1, it = 0, nbreak = 0;
+    double resid = 0.0;
+    bool done = !has;
+    if (has) {
+      if (!is_finite_bits(bb)) {
+        st = CAMP_CELL_NONFINITE;
+        resid = __longlong_as_double(0x7ff8000000000000ll);
+        done = true;
+      } else if (bb == 0.0) {
+        st = CAMP_CELL_CONVERGED;
+        done = true;
+#pragma unroll
+        for (int e = 0; e < E; ++e) xv[e] = 0.0;
+      }
+    }
+    if (a.x0_given) {  // r = b - A x0
+#pragma unroll
+      for (int e = 0; e < E; ++e) gs[sl + e * Lc] = xv[e];
+      __syncwarp();
+      seg_spmv(sch, a.L, Lc, As, gs, o1);
+      __syncwarp();
+#pragma unroll
+      for (int e = 0; e < E; ++e) r[e] -= o1[sl + e * Lc];
+    }
+
+    bool restart = !done, first = true;
+    bool fin = false, active = false, broke = false, nonfin = false;
+    double rho = 1.0, rho_prev = 1.0, alpha = 1.0, omega = 1.0;
+    for (;;) {
+      {  // (re)start from the current residual r
+        double acc[1] = {0.0};
+#pragma unroll
+        for (int e = 0; e < E; ++e) acc[0] = fma(r[e], r[e], acc[0]);
+        seg_sum<1>(acc, Lc);
+        if (restart) {
+#pragma unroll
+          for (int e = 0; e < E; ++e) {
+            rh[e] = r[e];
+            p[e] = 0.0;
+          }
+          rho = acc[0];
+          rho_prev = alpha = omega = 1.0;
+          broke = nonfin = false;
+          fin = true;
+          // a restart follows a failed true-residual test: always iterate
+          active = first ? !le_nonneg(acc[0], thr) : true;
+          restart = false;
+          first = false;
+        }
+      }
+      while (__any_sync(kFull, active)) {
+        if (active) {
+          if (it >= a.maxit) {
+            active = false;
+          } else if (!is_finite_bits(rho)) {
+            nonfin = true;
+            active = false;
+          } else if (abs_tiny(rho)) {
+            broke = true;
+            active = false;
+          }
+        }
+        // p = r + beta (p - omega v); the bracket is kept in p
+        const double beta = (rho / rho_prev) * (alpha / omega);
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+          if (active) p[e] = fma(beta, p[e], r[e]);
+          gs[sl + e * Lc] = dinv[e] * p[e];
+        }
+        __syncwarp();
+        seg_spmv(sch, a.L, Lc, As, gs, o1);  // v = A p^
+        __syncwarp();
+        if (active) ++it;
+        double sg[1] = {0.0};
+#pragma unroll
+        for (int e = 0; e < E; ++e) sg[0] = fma(rh[e], o1[sl + e * Lc], sg[0]);
+        seg_sum<1>(sg, Lc);
+        if (active) {
+          if (!is_finite_bits(sg[0])) {
+            nonfin = true;
+            active = false;
+          } else if (abs_tiny(sg[0])) {
+            broke = true;
+            active = false;
+          }
+        }
+        const double al = rho / sg[0];
+        if (active) alpha = al;
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+          const int i = sl + e * Lc;
+          if (active) {
+            xv[e] = fma(al, gs[i], xv[e]);
+            s[e] = fma(-al, o1[i], r[e]);
+          }
+          gs[i] = dinv[e] * s[e];
+        }
+        __syncwarp();
+        seg_spmv(sch, a.L, Lc, As, gs, o2);  // t = A s^
+        __syncwarp();
+        double q3[3] = {0.0, 0.0, 0.0};
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+          const double t = o2[sl + e * Lc];
+          q3[0] = fma(s[e], s[e], q3[0]);
+          q3[1] = fma(t, s[e], q3[1]);
+          q3[2] = fma(t, t, q3[2]);
+        }
+        seg_sum<3>(q3, Lc);
+        bool full = false;
+        if (active) {
+          if (le_nonneg(q3[0], thr)) {
+            active = false;  // converged on the half step (x has alpha p^)
+          } else if (!is_finite_bits(q3[1]) || !is_finite_bits(q3[2])) {
+            nonfin = true;
+            active = false;
+          } else if (q3[2] == 0.0) {
+            broke = true;  // keep the half step, restart
+            active = false;
+          } else {
+            full = true;
+          }
+        }
+        const double om = q3[1] / q3[2];
+        if (full) omega = om;
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+          const int i = sl + e * Lc;
+          if (full) {
+            xv[e] = fma(om, gs[i], xv[e]);
+            r[e] = fma(-om, o2[i], s[e]);
+            p[e] = fma(-om, o1[i], p[e]);
+          }
+        }
+        double q2[2] = {0.0, 0.0};
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+          q2[0] = fma(rh[e], r[e], q2[0]);
+          q2[1] = fma(r[e], r[e], q2[1]);
+        }
+        seg_sum<2>(q2, Lc);
+        if (full) {
+          nbreak = 0;
+          if (le_nonneg(q2[1], thr)) {
+            active = false;
+          } else if (om == 0.0) {
+            broke = true;
+            active = false;
+          } else {
+            rho_prev = rho;
+            rho = q2[0];
+          }
+        }
+      }
+      // ---- true residual of the segments that stopped iterating
+#pragma unroll
+      for (int e = 0; e < E; ++e) gs[sl + e * Lc] = xv[e];
+      __syncwarp();
+      seg_spmv(sch, a.L, Lc, As, gs, o1);
+      __syncwarp();
+      double rt2[1] = {0.0};
+      double rt[E];
+#pragma unroll
+      for (int e = 0; e < E; ++e) {
+        const int i = sl + e * Lc;
+        const double bi = (has && i < n) ? __ldg(a.b + (size_t)c * n + i) : 0.0;
+        rt[e] = bi - o1[i];
+        rt2[0] = fma(rt[e], rt[e], rt2[0]);
+      }
+      seg_sum<1>(rt2, Lc);
+      if (fin) {
+        fin = false;
+        resid = sqrt(rt2[0]) / bnorm;
+        if (nonfin || !is_finite_bits(resid)) {
+          st = CAMP_CELL_NONFINITE;
+        } else if (resid <= tol) {
+          st = CAMP_CELL_CONVERGED;
+        } else if (it >= a.maxit) {
+          st = CAMP_CELL_MAXIT;
+        } else if (broke && ++nbreak >= 2) {
+          st = CAMP_CELL_BREAKDOWN;
+        } else {
+#pragma unroll
+          for (int e = 0; e < E; ++e) r[e] = rt[e];
+          restart = true;
+        }
+        if (!restart) done = true;
+      }
+      if (!__any_sync(kFull, restart)) break;
+    }
+    // ---- write the cell's results
+    if (has) {
+#pragma unroll
+      for (int e = 0; e < E; ++e) {
+        const int i = sl + e * Lc;
+        if (i < n) a.x[(size_t)c * n + i] = xv[e];
+      }
+      if (sl == 0) {
+        a.iters[c] = it;
+        a.resid[c] = resid;
+        if (a.status) a.status[c] = st;
+      }
+    }
+    __syncwarp();
+  }
+}
+
+}  // namespace camp
