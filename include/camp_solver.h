@@ -172,6 +172,23 @@ camp_status camp_solver_solve_mixed(camp_solver_t h, int cells,
                                     int *iters_out, int *sweeps_out,
                                     double *resid_out, int *status_out);
 
+/*
+ * Inspect the static SpMV schedule the warp-packed kernels use for a pattern
+ * (host only, no GPU needed).  The rows are assigned whole to lanes_per_cell
+ * lanes by longest-first bin packing; each lane runs slots_per_lane slots.
+ * words (host, may be NULL to query slots_per_lane only) receives
+ * slots_per_lane * lanes_per_cell slots laid out [slot][lane], two uint32 per
+ * slot: word0 = entry index k | column << 16, word1 = row | 1 << 16 on the
+ * last entry of a row (store the running sum to that row), else 0; padding
+ * slots are (0, 0) and their sums are discarded.  capacity_slots is the
+ * number of slots words can hold.  Pattern requirements as for
+ * camp_solver_create (validation is lighter: sizes only).
+ */
+camp_status camp_schedule_build(int n, int nnz, const int *row_ptr,
+                                const int *col_idx, int lanes_per_cell,
+                                unsigned *words, int capacity_slots,
+                                int *slots_per_lane);
+
 /* Thread-local message describing the last error (never NULL). */
 const char *camp_last_error(void);
 

@@ -75,3 +75,29 @@ cudaError_t launch_grad(const GradArgs &a, cudaStream_t st);
 constexpr int kMaxE = 16;  // rows per lane supported by the warp kernel
 
 }  // namespace camp
+
+namespace camp {
+// Arguments of the FP32-inner / FP64-outer refinement kernel (warp-packed
+// layout as WarpArgs).
+struct MixedArgs {
+  int cells, n, nnz;
+  int Lc, log2Lc, k, L;
+  int segA, segV;
+  int ngroups;
+  const double *A, *b;
+  double *x;
+  int *iters;     // total inner FP32 iterations
+  int *sweeps;    // outer sweeps (or null)
+  double *resid;  // final FP64 true relative residual
+  int *status;    // or null
+  const int *diag;
+  const SchedWord *sched;
+  double tol;
+  int max_sweeps;
+  float tol_in;
+  int maxit_in;
+};
+cudaError_t launch_mixed(int E, const MixedArgs &a, int warps_per_block,
+                         int grid, size_t smem, cudaStream_t st);
+cudaError_t mixed_occupancy(int E, int warps_per_block, size_t smem, int *blocks);
+}  // namespace camp

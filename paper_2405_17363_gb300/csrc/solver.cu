@@ -22,6 +22,14 @@ CAMP_DECL(2) CAMP_DECL(3) CAMP_DECL(4) CAMP_DECL(5) CAMP_DECL(6) CAMP_DECL(7)
 CAMP_DECL(8) CAMP_DECL(9) CAMP_DECL(10) CAMP_DECL(11) CAMP_DECL(12)
 CAMP_DECL(13) CAMP_DECL(14) CAMP_DECL(15) CAMP_DECL(16)
 cudaError_t occ_warp_1(int, size_t, int *);
+#define CAMP_DECLM(E)                                                        \
+  cudaError_t launch_mixed_##E(const MixedArgs &, int, int, size_t, cudaStream_t); \
+  cudaError_t occ_mixed_##E(int, size_t, int *);
+CAMP_DECLM(1) CAMP_DECLM(2) CAMP_DECLM(3) CAMP_DECLM(4) CAMP_DECLM(5)
+CAMP_DECLM(6) CAMP_DECLM(7) CAMP_DECLM(8) CAMP_DECLM(9) CAMP_DECLM(10)
+CAMP_DECLM(11) CAMP_DECLM(12) CAMP_DECLM(13) CAMP_DECLM(14) CAMP_DECLM(15)
+CAMP_DECLM(16)
+#undef CAMP_DECLM
 #undef CAMP_DECL
 
 cudaError_t launch_warp(int E, const WarpArgs &a, int wpb, int grid,
@@ -37,6 +45,26 @@ cudaError_t launch_warp(int E, const WarpArgs &a, int wpb, int grid,
 cudaError_t warp_occupancy(int E, int wpb, size_t smem, int *blocks) {
   switch (E) {
 #define C(E) case E: return occ_warp_##E(wpb, smem, blocks);
+    C(1) C(2) C(3) C(4) C(5) C(6) C(7) C(8) C(9) C(10) C(11) C(12) C(13)
+    C(14) C(15) C(16)
+#undef C
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t launch_mixed(int E, const MixedArgs &a, int wpb, int grid,
+                         size_t smem, cudaStream_t st) {
+  switch (E) {
+#define C(E) case E: return launch_mixed_##E(a, wpb, grid, smem, st);
+    C(1) C(2) C(3) C(4) C(5) C(6) C(7) C(8) C(9) C(10) C(11) C(12) C(13)
+    C(14) C(15) C(16)
+#undef C
+    default: return cudaErrorInvalidValue;
+  }
+}
+cudaError_t mixed_occupancy(int E, int wpb, size_t smem, int *blocks) {
+  switch (E) {
+#define C(E) case E: return occ_mixed_##E(wpb, smem, blocks);
     C(1) C(2) C(3) C(4) C(5) C(6) C(7) C(8) C(9) C(10) C(11) C(12) C(13)
     C(14) C(15) C(16)
 #undef C
@@ -71,7 +99,8 @@ struct Schedule {
   SchedWord *d_words = nullptr;
 };
 
-Schedule build_schedule(int n, const std::vector<int> &rp, int Lc) {
+Schedule build_schedule(int n, const std::vector<int> &rp,
+                        const std::vector<int> &ci, int Lc) {
   std::vector<int> order(n);
   std::iota(order.begin(), order.end(), 0);
   std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
@@ -96,7 +125,7 @@ Schedule build_schedule(int n, const std::vector<int> &rp, int Lc) {
     for (int r : rows[q])
       for (int k = rp[r]; k < rp[r + 1]; ++k, ++j) {
         SchedWord w;
-        w.x = (unsigned)k | ((unsigned)0 << 16);
+        w.x = (unsigned)k | ((unsigned)ci[k] << 16);
         w.y = (k == rp[r + 1] - 1) ? ((unsigned)r | (1u << 16)) : 0u;
         S.words[(size_t)j * Lc + q] = w;
       }
@@ -149,7 +178,7 @@ namespace {
 cudaError_t view_schedule(View &v, int Lc, Schedule **out) {
   auto it = v.sched.find(Lc);
   if (it == v.sched.end()) {
-    Schedule S = build_schedule(v.n, v.rp, Lc);
+    Schedule S = build_schedule(v.n, v.rp, v.ci, Lc);
     cudaError_t e = upload(&S.d_words, S.words);
     if (e != cudaSuccess) return e;
     it = v.sched.emplace(Lc, std::move(S)).first;
@@ -188,6 +217,15 @@ size_t warp_smem(const View &v, int Lc, int L, int wpb, int *segA, int *segV) {
 double warp_cost(int Lc, int L, int E) {
   const int k = 32 / Lc;
   return (2.0 * L + 14.0 * E + 6.0 * ilog2(Lc) + 30.0) / k;
+}
+
+size_t mixed_smem(const View &v, int Lc, int L, int wpb, int *segA, int *segV) {
+  const int k = 32 / Lc;
+  const int E = (v.n + Lc - 1) / Lc;
+  *segA = (v.nnz + 1) & ~1;
+  *segV = ((E * Lc + 1) + 1) & ~1;
+  const size_t sch = (((size_t)L * Lc * 8) + 15) & ~(size_t)15;
+  return sch + (size_t)wpb * k * ((size_t)12 * *segA + (size_t)28 * *segV);
 }
 
 size_t block_smem(int n, int nnz, int cpb, int threads) {
@@ -298,6 +336,32 @@ extern "C" {
 
 const char *camp_last_error(void) { return g_err.c_str(); }
 const char *camp_version(void) { return "campsolve 0.1 (sm_103a)"; }
+
+camp_status camp_schedule_build(int n, int nnz, const int *row_ptr,
+                                const int *col_idx, int lanes_per_cell,
+                                unsigned *words, int capacity_slots,
+                                int *slots_per_lane) {
+  if (!row_ptr || !col_idx || !slots_per_lane)
+    return fail(CAMP_EINVAL, "null argument");
+  if (n < 1 || nnz < n || nnz > 65535 || row_ptr[n] != nnz)
+    return fail(CAMP_EINVAL, "bad sizes");
+  if (lanes_per_cell < 1 || lanes_per_cell > 32 ||
+      (lanes_per_cell & (lanes_per_cell - 1)))
+    return fail(CAMP_EINVAL, "lanes_per_cell must be a power of two in [1, 32]");
+  std::vector<int> rp(row_ptr, row_ptr + n + 1), ci(col_idx, col_idx + nnz);
+  Schedule S = build_schedule(n, rp, ci, lanes_per_cell);
+  *slots_per_lane = S.L;
+  if (words) {
+    if ((long)S.L * lanes_per_cell > (long)capacity_slots)
+      return fail(CAMP_EINVAL, "capacity %d < %d slots", capacity_slots,
+                  S.L * lanes_per_cell);
+    for (size_t q = 0; q < S.words.size(); ++q) {
+      words[2 * q] = S.words[q].x;
+      words[2 * q + 1] = S.words[q].y;
+    }
+  }
+  return CAMP_OK;
+}
 
 camp_status camp_solver_create(camp_solver_t *out, int n, int nnz,
                                const int *row_ptr, const int *col_idx) {
@@ -547,11 +611,57 @@ camp_status camp_solver_solve_mixed(camp_solver_t h, int cells,
                                     double tol_inner, int maxit_inner,
                                     int *iters_out, int *sweeps_out,
                                     double *resid_out, int *status_out) {
-  (void)cells; (void)A_vals; (void)b; (void)x; (void)tol; (void)max_sweeps;
-  (void)tol_inner; (void)maxit_inner; (void)iters_out; (void)sweeps_out;
-  (void)resid_out; (void)status_out;
   if (!h) return fail(CAMP_EINVAL, "null solver handle");
-  return fail(CAMP_EUNSUPPORTED, "mixed precision kernel not built yet");
+  if (cells < 0) return fail(CAMP_EINVAL, "cells < 0");
+  if (!(tol > 0.0) || !std::isfinite(tol)) return fail(CAMP_EINVAL, "tol must be finite and > 0");
+  if (!(tol_inner > 0.0) || !(tol_inner < 1.0)) return fail(CAMP_EINVAL, "tol_inner must be in (0, 1)");
+  if (max_sweeps < 1 || maxit_inner < 1) return fail(CAMP_EINVAL, "max_sweeps and maxit_inner must be >= 1");
+  if (cells == 0) return CAMP_OK;
+  if (!A_vals || !b || !x || !iters_out || !resid_out)
+    return fail(CAMP_EINVAL, "null array pointer");
+  cudaError_t e = cudaSetDevice(h->device);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
+  View &v = h->fwd;
+  int Lc = (h->arrangement == CAMP_ARR_WARP) ? h->lanes : 0;
+  if (Lc == 0) {
+    double best = 1e300;
+    for (int cand = 1; cand <= 32; cand *= 2) {
+      const int E = (v.n + cand - 1) / cand;
+      if (E > kMaxE) continue;
+      Schedule *S = nullptr;
+      if ((e = view_schedule(v, cand, &S)) != cudaSuccess) return cuda_fail(e, "schedule upload");
+      int sa, sv;
+      if (mixed_smem(v, cand, S->L, 1, &sa, &sv) > h->smem_optin) continue;
+      const double cst = warp_cost(cand, S->L, E);
+      if (cst < best) { best = cst; Lc = cand; }
+    }
+    if (Lc == 0) return fail(CAMP_EUNSUPPORTED, "no warp arrangement fits n=%d", v.n);
+  }
+  const int E = (v.n + Lc - 1) / Lc;
+  if (E > kMaxE) return fail(CAMP_EUNSUPPORTED, "n=%d too large for %d lanes per cell", v.n, Lc);
+  Schedule *S = nullptr;
+  if ((e = view_schedule(v, Lc, &S)) != cudaSuccess) return cuda_fail(e, "schedule upload");
+  int wpb = h->wpb > 0 ? h->wpb : 4;
+  int segA = 0, segV = 0;
+  size_t smem = mixed_smem(v, Lc, S->L, wpb, &segA, &segV);
+  while (smem > h->smem_optin && wpb > 1) smem = mixed_smem(v, Lc, S->L, --wpb, &segA, &segV);
+  if (smem > h->smem_optin) return fail(CAMP_EUNSUPPORTED, "cell does not fit in shared memory");
+  MixedArgs a;
+  a.cells = cells; a.n = v.n; a.nnz = v.nnz;
+  a.Lc = Lc; a.log2Lc = ilog2(Lc); a.k = 32 / Lc; a.L = S->L;
+  a.segA = segA; a.segV = segV; a.ngroups = (cells + a.k - 1) / a.k;
+  a.A = A_vals; a.b = b; a.x = x; a.iters = iters_out; a.sweeps = sweeps_out;
+  a.resid = resid_out; a.status = status_out; a.diag = v.d_diag; a.sched = S->d_words;
+  a.tol = tol; a.max_sweeps = max_sweeps; a.tol_in = (float)tol_inner;
+  a.maxit_in = maxit_inner;
+  int occ = 0;
+  if ((e = mixed_occupancy(E, wpb, smem, &occ)) != cudaSuccess) return cuda_fail(e, "occupancy");
+  if (occ < 1) occ = 1;
+  const int need = (a.ngroups + wpb - 1) / wpb;
+  const int grid = std::max(1, std::min(need, h->sms * occ));
+  if ((e = launch_mixed(E, a, wpb, grid, smem, h->stream)) != cudaSuccess)
+    return cuda_fail(e, "mixed kernel launch");
+  return CAMP_OK;
 }
 
 }  // extern "C"

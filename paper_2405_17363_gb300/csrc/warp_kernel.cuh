@@ -17,52 +17,9 @@
 // s and r, true-residual check with residual replacement, breakdown and
 // non-finite rules, iteration count = products v = A p^).
 #pragma once
-#include "camp_internal.h"
+#include "warp_common.cuh"
 
 namespace camp {
-
-constexpr unsigned kFull = 0xffffffffu;
-
-__device__ __forceinline__ bool is_finite_bits(double v) {
-  const unsigned long long u = (unsigned long long)__double_as_longlong(v);
-  return ((u >> 52) & 0x7ffull) != 0x7ffull;
-}
-// |v| < 1e-300, on the bit pattern (no FP64 instruction)
-__device__ __forceinline__ bool abs_tiny(double v) {
-  const unsigned long long u =
-      (unsigned long long)__double_as_longlong(v) & 0x7fffffffffffffffull;
-  return u < 0x01a56e1fc2f8f359ull;  // bit pattern of 1e-300
-}
-// a <= b for a, b >= +0 (or NaN a: false), on the bit pattern
-__device__ __forceinline__ bool le_nonneg(double a, double b) {
-  return __double_as_longlong(a) <= __double_as_longlong(b);
-}
-
-// Sum NV values over the Lc lanes of each segment (xor butterfly; every lane
-// of the segment ends with the same bits).
-template <int NV>
-__device__ __forceinline__ void seg_sum(double (&v)[NV], int Lc) {
-  for (int off = Lc >> 1; off > 0; off >>= 1) {
-#pragma unroll
-    for (int q = 0; q < NV; ++q) v[q] += __shfl_xor_sync(kFull, v[q], off);
-  }
-}
-
-// o[row] = sum_k A_s[k] g[col k] over this lane's slots of the schedule.
-__device__ __forceinline__ void seg_spmv(const SchedWord *__restrict__ sch,
-                                         int L, int Lc, const double *As,
-                                         const double *gs, double *os) {
-  double acc = 0.0;
-#pragma unroll 4
-  for (int j = 0; j < L; ++j) {
-    const SchedWord w = sch[j * Lc];
-    acc = fma(As[w.x & 0xffffu], gs[w.x >> 16], acc);
-    if (w.y >> 16) {
-      os[w.y & 0xffffu] = acc;
-      acc = 0.0;
-    }
-  }
-}
 
 template <int E>
 __global__ void __launch_bounds__(256)
