@@ -159,6 +159,71 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def set_arrangement(camp, solver, spec):
+    parts = spec.split(":")
+    if parts[0] == "auto":
+        return "auto"
+    if parts[0] == "warp":
+        lc = int(parts[1])
+        wpb = int(parts[2]) if len(parts) > 2 else 0
+        solver.set_arrangement(camp.CAMP_ARR_WARP, lc, 0, wpb)
+        return f"warp-packed, {lc} lanes per cell, {32 // lc} cells per warp"
+    if parts[0] == "block":
+        cpb = int(parts[1])
+        solver.set_arrangement(camp.CAMP_ARR_BLOCK, 0, cpb, 0)
+        return f"Block-cells({cpb}): one thread per row"
+    raise SystemExit(f"bad --arrangement {spec}")
+
+
+def time_steps(fn, flush, stream, steps, warmup):
+    """CUDA-event time of each step on the launching stream; the L2 flush
+    between steps is outside the events.  Returns the per-step times (ms)."""
+    import torch
+    for _ in range(warmup):
+        flush.zero_()
+        fn()
+    torch.cuda.synchronize()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(steps)]
+    for k in range(steps):
+        flush.zero_()
+        evs[k][0].record(stream)
+        fn()
+        evs[k][1].record(stream)
+    torch.cuda.synchronize()
+    return [a.elapsed_time(b) for a, b in evs]
+
+
+def time_e2e(camp, solver, cb, C, tol, maxit, steps, world, dev):
+    """Same metric end to end through the public host-memory entry point:
+    every step copies A_vals and b from pinned host memory and copies x,
+    iters, resid and status back."""
+    import torch
+    import torch.distributed as dist
+    m = cb.mech
+    hA = torch.as_tensor(cb.A_vals).pin_memory()
+    hb = torch.as_tensor(cb.b).pin_memory()
+    hx = torch.empty((C, m.n), dtype=torch.float64).pin_memory()
+    hit = torch.empty(C, dtype=torch.int32).pin_memory()
+    hres = torch.empty(C, dtype=torch.float64).pin_memory()
+    hst = torch.empty(C, dtype=torch.int32).pin_memory()
+    for _ in range(3):
+        camp.camp_solver_solve_host(solver.h, C, hA, hb, hx, tol, maxit, hit, hres, hst)
+    if world > 1:
+        dist.barrier()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        camp.camp_solver_solve_host(solver.h, C, hA, hb, hx, tol, maxit, hit, hres, hst)
+    el = time.perf_counter() - t0
+    if world > 1:
+        t = torch.tensor([el], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        el = float(t.item())
+    return {"value": world * C * steps / el, "unit": UNIT,
+            "h2d_bytes_per_step": C * (m.nnz + m.n) * 8,
+            "d2h_bytes_per_step": C * (m.n * 8 + 4 + 8 + 4)}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -167,6 +232,12 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--e2e-steps", type=int, default=50)
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--arrangement", default="auto",
+                    help="auto | warp:<lanes per cell>[:<warps per block>] | block:<cells per block>")
+    ap.add_argument("--mode", default="fp64", choices=["fp64", "mixed"],
+                    help="fp64: plain FP64 solve (the headline); mixed: FP32-inner refinement")
+    ap.add_argument("--skip-extras", action="store_true",
+                    help="time the device solve only (no e2e, CPU baseline or mixed side run)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -192,81 +263,68 @@ def main():
     m = cb.mech
     C = cb.cells
     solver = camp.Solver(m.row_ptr, m.col_idx)
+    arr_desc = set_arrangement(camp, solver, args.arrangement)
     A = torch.as_tensor(cb.A_vals, device=dev)
     b = torch.as_tensor(cb.b, device=dev)
     x = torch.empty((C, m.n), dtype=torch.float64, device=dev)
     it = torch.empty(C, dtype=torch.int32, device=dev)
     res = torch.empty(C, dtype=torch.float64, device=dev)
     st = torch.empty(C, dtype=torch.int32, device=dev)
+    sweeps = torch.empty(C, dtype=torch.int32, device=dev)
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)   # > 129 MB L2
     stream = torch.cuda.current_stream()
 
-    def step():
+    def solve_fp64():
         camp.camp_solver_solve_ex(solver.h, C, A, b, x, tol, maxit, it, res, st, 0)
 
-    for _ in range(args.warmup):
-        flush.zero_()
-        step()
-    torch.cuda.synchronize()
+    def solve_mixed():
+        camp.camp_solver_solve_mixed(solver.h, C, A, b, x, tol, 20, 1e-5, 50, it, sweeps,
+                                     res, st)
 
-    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-           for _ in range(args.steps)]
+    step = solve_fp64 if args.mode == "fp64" else solve_mixed
     clocks = ClockSampler(local)
     clocks.start()
     time.sleep(0.3)
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
-    for k in range(args.steps):
-        flush.zero_()
-        evs[k][0].record(stream)
-        step()
-        evs[k][1].record(stream)
-    torch.cuda.synchronize()
+    times = time_steps(step, flush, stream, args.steps, args.warmup)
     if world > 1:
         dist.barrier()
     clk = clocks.stop()
-    times = [e0.elapsed_time(e1) for e0, e1 in evs]   # ms
     total_ms = float(sum(times))
     if world > 1:
         t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         total_ms = float(t.item())
-
     iters = it.cpu().numpy()
     status = st.cpu().numpy()
+    sw = sweeps.cpu().numpy()
     value = world * C * args.steps / (total_ms * 1e-3)
     ms_step = total_ms / args.steps
-    flops, nbytes = algorithmic(m, C, iters)
-    hbm_peak, hbm_src = peaks()
     kernel_s = ms_step * 1e-3
+    hbm_peak, hbm_src = peaks()
+    flops, nbytes = algorithmic(m, C, iters)
 
-    # end to end through the public API from pinned host memory
-    hA = torch.as_tensor(cb.A_vals).pin_memory()
-    hb = torch.as_tensor(cb.b).pin_memory()
-    hx = torch.empty((C, m.n), dtype=torch.float64).pin_memory()
-    hit = torch.empty(C, dtype=torch.int32).pin_memory()
-    hres = torch.empty(C, dtype=torch.float64).pin_memory()
-    hst = torch.empty(C, dtype=torch.int32).pin_memory()
-    for _ in range(3):
-        camp.camp_solver_solve_host(solver.h, C, hA, hb, hx, tol, maxit, hit, hres, hst)
-    if world > 1:
-        dist.barrier()
-    t0 = time.perf_counter()
-    for _ in range(args.e2e_steps):
-        camp.camp_solver_solve_host(solver.h, C, hA, hb, hx, tol, maxit, hit, hres, hst)
-    e2e_s = time.perf_counter() - t0
-    if world > 1:
-        t = torch.tensor([e2e_s], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
-    e2e = {"value": world * C * args.e2e_steps / e2e_s, "unit": UNIT,
-           "h2d_bytes_per_step": C * (m.nnz + m.n) * 8,
-           "d2h_bytes_per_step": C * (m.n * 8 + 4 + 8 + 4)}
+    mixed_side = None
+    e2e = None
+    if not args.skip_extras:
+        if args.mode == "fp64":
+            mt = time_steps(solve_mixed, flush, stream, 200, 5)
+            mms = sum(mt) / len(mt)
+            mixed_side = {
+                "value": world * C / (mms * 1e-3), "unit": UNIT, "ms_per_step": mms,
+                "what": "FP32-inner BiCGSTAB with FP64 residual and refinement sweeps "
+                        "to the same 1e-10 true residual",
+                "sweeps_mean": float(sweeps.float().mean().item()),
+                "inner_iters_mean": float(it.float().mean().item()),
+                "converged": int((st == 0).sum().item()),
+                "speedup_vs_fp64": ms_step / mms}
+        e2e = time_e2e(camp, solver, cb, C, tol, maxit, args.e2e_steps, world, dev)
 
     if rank == 0:
         cpu = cpu_baseline(m, cb.A_vals, cb.b, tol, maxit, args.cpu_seconds) \
-            if world == 1 else None
+            if world == 1 and not args.skip_extras else None
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
@@ -274,7 +332,7 @@ def main():
             "dtype": "f64", "data": "synthetic",
             "config": {"workload": synth.WORKLOADS[WORKLOAD_ID][0], "cells": C,
                        "n": m.n, "nnz": m.nnz, "tol": tol, "maxit": maxit,
-                       "arrangement": "auto (warp-packed)",
+                       "mode": args.mode, "arrangement": arr_desc,
                        "l2": "flushed between timed steps (512 MB write)",
                        "iters_max": int(iters.max()), "iters_mean": float(iters.mean()),
                        "converged": int((status == 0).sum())},
@@ -291,6 +349,11 @@ def main():
             "gpu_launches": args.steps,
             "clocks": clk,
         }
+        if args.mode == "mixed":
+            line["config"]["sweeps_mean"] = float(sw.mean())
+            line["roofline"] = None
+        if mixed_side is not None:
+            line["mixed_fp32_inner"] = mixed_side
         if cpu is not None:
             line["cpu_baseline"] = cpu
         print(json.dumps(line), flush=True)
