@@ -14,7 +14,7 @@ import os
 import torch
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "_lib", "libcampsolve.so")
+LIB_PATH = os.environ.get("CAMP_LIBRARY") or os.path.join(_HERE, "_lib", "libcampsolve.so")
 
 if not os.path.exists(LIB_PATH):
     raise ImportError(f"libcampsolve.so is not built ({LIB_PATH}); run "

@@ -22,6 +22,7 @@ struct WarpArgs {
   int Lc, log2Lc, k;       // lanes per cell, log2, cells per warp
   int L;                   // schedule slots per lane
   int segA, segV;          // shared-memory doubles per cell: A block, one vector
+  int segStride;           // doubles from one cell's block to the next (bank-spread)
   int ngroups;             // ceil(cells / k)
   const double *A, *b;     // [cells x nnz], [cells x n]
   double *x;               // [cells x n]
@@ -73,6 +74,9 @@ cudaError_t block_set_smem(size_t smem);
 cudaError_t launch_grad(const GradArgs &a, cudaStream_t st);
 
 constexpr int kMaxE = 16;  // rows per lane supported by the warp kernel
+// vectors of n (padded) doubles per cell in the warp kernel's shared memory:
+// gathered vector, two products, shadow residual, Jacobi reciprocals
+constexpr int kWarpVectors = 5;
 
 }  // namespace camp
 

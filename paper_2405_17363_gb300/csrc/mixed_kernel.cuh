@@ -14,7 +14,7 @@
 namespace camp {
 
 template <int E>
-__global__ void __launch_bounds__(256) mixed_refine_kernel(const MixedArgs a) {
+__global__ void __launch_bounds__(256, 2) mixed_refine_kernel(const MixedArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   SchedWord *sch_s = reinterpret_cast<SchedWord *>(smem_raw);
   const int nsch = a.L * a.Lc;
@@ -73,7 +73,7 @@ __global__ void __launch_bounds__(256) mixed_refine_kernel(const MixedArgs a) {
       seg_sum<1>(acc, Lc);
       bb = acc[0];
     }
-    const double bnorm = sqrt(bb);
+    const double thr = (a.tol * a.tol) * bb;  // (tol ||b||)^2
     int st = -1, sweeps = 0, inner = 0;
     double resid = 0.0;
     bool done = !has;
@@ -81,7 +81,7 @@ __global__ void __launch_bounds__(256) mixed_refine_kernel(const MixedArgs a) {
       st = CAMP_CELL_NONFINITE;
       resid = __longlong_as_double(0x7ff8000000000000ll);
       done = true;
-    } else if (has && bb == 0.0) {
+    } else if (has && is_zero_bits(bb)) {
       st = CAMP_CELL_CONVERGED;
       done = true;
     }
@@ -105,27 +105,40 @@ __global__ void __launch_bounds__(256) mixed_refine_kernel(const MixedArgs a) {
       }
       seg_sum<1>(rr, Lc);
       if (!done) {
-        resid = sqrt(rr[0]) / bnorm;
-        if (!is_finite_bits(resid)) {
+        // ||r|| <= tol ||b|| on the bit patterns; the relative residual itself
+        // (a square root and a division) is formed once, at the end
+        if (!is_finite_bits(rr[0])) {
           st = CAMP_CELL_NONFINITE;
           done = true;
-        } else if (resid <= a.tol) {
+        } else if (le_nonneg(rr[0], thr)) {
           st = CAMP_CELL_CONVERGED;
           done = true;
         } else if (sweeps >= a.max_sweeps) {
           st = CAMP_CELL_MAXIT;
           done = true;
         }
+        if (done) resid = sqrt(rr[0] * recip64(bb));
       }
       if (!__any_sync(kFull, !done)) break;
-      // ---- FP32 inner solve of A d = r / ||r||
-      const double rn = sqrt(rr[0]);
-      const double scale = 1.0 / rn;
+      // ---- FP32 inner solve of A d = r / ||r||.  The scale only sets the
+      // size of the FP32 right-hand side, so it is formed in FP32 (FP64 when
+      // ||r||^2 is outside the FP32 range).
+      float rn32, rinv32;
+      bool wide = false;
+      {
+        const int ex = (int)(((unsigned long long)__double_as_longlong(rr[0]) >> 52) & 0x7ffull) - 1023;
+        wide = ex < -120 || ex > 120;
+        const float rr32 = d2f_rn(rr[0]);
+        rinv32 = rsqrtf(rr32);
+        rn32 = rr32 * rinv32;
+      }
+      const double rn64 = wide ? sqrt(rr[0]) : 0.0;
+      const double sc64 = wide ? 1.0 / rn64 : 0.0;
       float rf[E], rh[E], p[E], s[E], d[E];
       float cc[1] = {0.0f};
 #pragma unroll
       for (int e = 0; e < E; ++e) {
-        const float ce = done ? 0.0f : d2f_rn(r[e] * scale);
+        const float ce = done ? 0.0f : (wide ? d2f_rn(r[e] * sc64) : d2f_rn(r[e]) * rinv32);
         rf[e] = ce;
         rh[e] = ce;
         p[e] = 0.0f;
@@ -218,7 +231,8 @@ __global__ void __launch_bounds__(256) mixed_refine_kernel(const MixedArgs a) {
         inner += it;
         ++sweeps;
 #pragma unroll
-        for (int e = 0; e < E; ++e) xv[e] = fma(rn, f2d_exact(d[e]), xv[e]);
+        for (int e = 0; e < E; ++e)
+          xv[e] += wide ? rn64 * f2d_exact(d[e]) : f2d_exact(rn32 * d[e]);
       }
     }
     if (has) {

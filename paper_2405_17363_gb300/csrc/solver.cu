@@ -12,6 +12,9 @@
 #include <vector>
 
 #include "camp_internal.h"
+#ifndef CAMP_A_GLOBAL
+#define CAMP_A_GLOBAL 0
+#endif
 
 namespace camp {
 cudaError_t launch_warp_1(const WarpArgs &, int, int, size_t, cudaStream_t);
@@ -202,21 +205,31 @@ int ilog2(int v) {
   return l;
 }
 
-// Warp kernel shared-memory bytes for one CTA.
-size_t warp_smem(const View &v, int Lc, int L, int wpb, int *segA, int *segV) {
-  const int k = 32 / Lc;
-  const int E = (v.n + Lc - 1) / Lc;
-  *segA = (v.nnz + 1) & ~1;
-  *segV = ((E * Lc + 1) + 1) & ~1;
-  const size_t sch = (((size_t)L * Lc * 8) + 15) & ~(size_t)15;
-  return sch + (size_t)wpb * k * (*segA + 3 * *segV) * 8;
+// Doubles from one cell's shared-memory block to the next: at least `need`,
+// and offset modulo 16 doubles (one pass over the 32 four-byte banks) so that
+// the k cells of a warp, which read the same relative addresses in the same
+// instruction, start on different banks.
+int bank_spread_stride(int need, int k) {
+  const int want = k >= 16 ? 1 : 16 / k;
+  int s = need;
+  while (s % 16 != want % 16) ++s;
+  return s;
 }
 
-// Estimated FP64 warp-instructions per cell-iteration of the warp kernel
-// (used by the automatic arrangement choice).
-double warp_cost(int Lc, int L, int E) {
+// Warp kernel shared-memory bytes for one CTA.
+size_t warp_smem(const View &v, int Lc, int L, int wpb, int *segA, int *segV,
+                 int *segStride) {
   const int k = 32 / Lc;
-  return (2.0 * L + 14.0 * E + 6.0 * ilog2(Lc) + 30.0) / k;
+  const int E = (v.n + Lc - 1) / Lc;
+#if CAMP_A_GLOBAL
+  *segA = 0;
+#else
+  *segA = (v.nnz + 1) & ~1;
+#endif
+  *segV = ((E * Lc + 1) + 1) & ~1;
+  *segStride = bank_spread_stride(*segA + kWarpVectors * *segV, k);
+  const size_t sch = (((size_t)L * Lc * 8) + 15) & ~(size_t)15;
+  return sch + (size_t)wpb * k * (size_t)*segStride * 8;
 }
 
 size_t mixed_smem(const View &v, int Lc, int L, int wpb, int *segA, int *segV) {
@@ -226,6 +239,17 @@ size_t mixed_smem(const View &v, int Lc, int L, int wpb, int *segA, int *segV) {
   *segV = ((E * Lc + 1) + 1) & ~1;
   const size_t sch = (((size_t)L * Lc * 8) + 15) & ~(size_t)15;
   return sch + (size_t)wpb * k * ((size_t)12 * *segA + (size_t)28 * *segV);
+}
+
+// Automatic arrangement: the most cells per warp (fewest lanes per cell) that
+// keeps at most `rows` rows per lane; FP64 scalar work and reductions are
+// shared by the cells of a warp, while per-lane rows cost registers.
+constexpr int kAutoRowsPerLane = 5;
+constexpr int kAutoRowsPerLaneMixed = 3;
+int auto_lanes(int n, int rows) {
+  for (int cand = 1; cand <= 32; cand *= 2)
+    if ((n + cand - 1) / cand <= rows) return cand;
+  return (n + 31) / 32 <= kMaxE ? 32 : 0;
 }
 
 size_t block_smem(int n, int nnz, int cpb, int threads) {
@@ -253,25 +277,8 @@ camp_status do_solve(camp_solver_t h, int cells, const double *A_vals,
   int Lc = h->lanes;
   if (arr == CAMP_ARR_AUTO) {
     arr = CAMP_ARR_WARP;
-    double best = 1e300;
-    Lc = 0;
-    for (int cand = 1; cand <= 32; cand *= 2) {
-      const int E = (v.n + cand - 1) / cand;
-      if (E > kMaxE) continue;
-      Schedule *S = nullptr;
-      e = view_schedule(v, cand, &S);
-      if (e != cudaSuccess) return cuda_fail(e, "schedule upload");
-      int sa, sv;
-      if (warp_smem(v, cand, S->L, 1, &sa, &sv) > h->smem_optin) continue;
-      const double cst = warp_cost(cand, S->L, E);
-      if (cst < best) {
-        best = cst;
-        Lc = cand;
-      }
-    }
-    if (Lc == 0) {
-      arr = CAMP_ARR_BLOCK;
-    }
+    Lc = auto_lanes(v.n, kAutoRowsPerLane);
+    if (Lc == 0) arr = CAMP_ARR_BLOCK;
   }
 
   if (arr == CAMP_ARR_WARP) {
@@ -283,18 +290,18 @@ camp_status do_solve(camp_solver_t h, int cells, const double *A_vals,
     e = view_schedule(v, Lc, &S);
     if (e != cudaSuccess) return cuda_fail(e, "schedule upload");
     int wpb = h->wpb > 0 ? h->wpb : 4;
-    int segA = 0, segV = 0;
-    size_t smem = warp_smem(v, Lc, S->L, wpb, &segA, &segV);
+    int segA = 0, segV = 0, segStride = 0;
+    size_t smem = warp_smem(v, Lc, S->L, wpb, &segA, &segV, &segStride);
     while (smem > h->smem_optin && wpb > 1) {
       --wpb;
-      smem = warp_smem(v, Lc, S->L, wpb, &segA, &segV);
+      smem = warp_smem(v, Lc, S->L, wpb, &segA, &segV, &segStride);
     }
     if (smem > h->smem_optin)
       return fail(CAMP_EUNSUPPORTED, "cell does not fit in shared memory (%zu bytes)", smem);
     WarpArgs a;
     a.cells = cells; a.n = v.n; a.nnz = v.nnz;
     a.Lc = Lc; a.log2Lc = ilog2(Lc); a.k = 32 / Lc; a.L = S->L;
-    a.segA = segA; a.segV = segV;
+    a.segA = segA; a.segV = segV; a.segStride = segStride;
     a.ngroups = (cells + a.k - 1) / a.k;
     a.A = A_vals; a.b = b; a.x = x; a.iters = iters_out; a.resid = resid_out;
     a.status = status_out; a.a_perm = v.d_perm; a.diag = v.d_diag;
@@ -622,21 +629,8 @@ camp_status camp_solver_solve_mixed(camp_solver_t h, int cells,
   cudaError_t e = cudaSetDevice(h->device);
   if (e != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
   View &v = h->fwd;
-  int Lc = (h->arrangement == CAMP_ARR_WARP) ? h->lanes : 0;
-  if (Lc == 0) {
-    double best = 1e300;
-    for (int cand = 1; cand <= 32; cand *= 2) {
-      const int E = (v.n + cand - 1) / cand;
-      if (E > kMaxE) continue;
-      Schedule *S = nullptr;
-      if ((e = view_schedule(v, cand, &S)) != cudaSuccess) return cuda_fail(e, "schedule upload");
-      int sa, sv;
-      if (mixed_smem(v, cand, S->L, 1, &sa, &sv) > h->smem_optin) continue;
-      const double cst = warp_cost(cand, S->L, E);
-      if (cst < best) { best = cst; Lc = cand; }
-    }
-    if (Lc == 0) return fail(CAMP_EUNSUPPORTED, "no warp arrangement fits n=%d", v.n);
-  }
+  int Lc = (h->arrangement == CAMP_ARR_WARP) ? h->lanes : auto_lanes(v.n, kAutoRowsPerLaneMixed);
+  if (Lc == 0) return fail(CAMP_EUNSUPPORTED, "no warp arrangement fits n=%d", v.n);
   const int E = (v.n + Lc - 1) / Lc;
   if (E > kMaxE) return fail(CAMP_EUNSUPPORTED, "n=%d too large for %d lanes per cell", v.n, Lc);
   Schedule *S = nullptr;

@@ -7,6 +7,10 @@
 namespace camp {
 
 constexpr unsigned kFull = 0xffffffffu;
+#ifndef CAMP_SPMV_UNROLL
+#define CAMP_SPMV_UNROLL 4
+#endif
+constexpr int kSpmvUnroll = CAMP_SPMV_UNROLL;  // schedule slots in flight per lane
 
 __device__ __forceinline__ bool is_finite_bits(double v) {
   const unsigned long long u = (unsigned long long)__double_as_longlong(v);
@@ -33,12 +37,64 @@ __device__ __forceinline__ void seg_sum(double (&v)[NV], int Lc) {
   }
 }
 
+// Two sums over the segment with log2(Lc) FP64 additions instead of
+// 2 log2(Lc): at the first level each lane pair exchanges the value the other
+// keeps (the lower lane keeps a, the upper keeps b), then one value is summed;
+// a final exchange gives every lane both totals.
+__device__ __forceinline__ void seg_sum2(double &a, double &b, int Lc) {
+  if (Lc == 1) return;
+  const int half = Lc >> 1;
+  const bool up = (threadIdx.x & half) != 0;
+  double keep = up ? b : a;
+  const double send = up ? a : b;
+  keep += __shfl_xor_sync(kFull, send, half);
+  for (int off = half >> 1; off > 0; off >>= 1) keep += __shfl_xor_sync(kFull, keep, off);
+  const double other = __shfl_xor_sync(kFull, keep, half);
+  a = up ? other : keep;
+  b = up ? keep : other;
+}
+
+// Three sums (a fourth slot is zero) with two transposing levels: 2 + 1 +
+// (log2(Lc) - 2) FP64 additions for Lc >= 4.
+__device__ __forceinline__ void seg_sum3(double &a, double &b, double &c, int Lc) {
+  if (Lc < 4) {
+    double v[3] = {a, b, c};
+    seg_sum<3>(v, Lc);
+    a = v[0]; b = v[1]; c = v[2];
+    return;
+  }
+  const int h1 = Lc >> 1, h2 = Lc >> 2;
+  const bool u1 = (threadIdx.x & h1) != 0;
+  const bool u2 = (threadIdx.x & h2) != 0;
+  // level 1: lower half keeps (a, b), upper half keeps (c, 0)
+  double k0 = u1 ? c : a, k1 = u1 ? 0.0 : b;
+  const double s0 = u1 ? a : c, s1 = u1 ? b : 0.0;
+  k0 += __shfl_xor_sync(kFull, s0, h1);
+  k1 += __shfl_xor_sync(kFull, s1, h1);
+  // level 2: lower quarter keeps k0, upper keeps k1
+  double k = u2 ? k1 : k0;
+  const double s = u2 ? k0 : k1;
+  k += __shfl_xor_sync(kFull, s, h2);
+  for (int off = h2 >> 1; off > 0; off >>= 1) k += __shfl_xor_sync(kFull, k, off);
+  // lane classes (u1, u2): (0,0) a, (0,1) b, (1,0) c, (1,1) zero
+  const double x2 = __shfl_xor_sync(kFull, k, h2);
+  const double x1 = __shfl_xor_sync(kFull, k, h1);
+  const double x3 = __shfl_xor_sync(kFull, k, h1 | h2);
+  // the lane whose class is (p, q) holds: own k, x2 = (p, !q), x1 = (!p, q), x3 = (!p, !q)
+  const double va = (!u1 && !u2) ? k : (!u1 && u2) ? x2 : (u1 && !u2) ? x1 : x3;
+  const double vb = (!u1 && u2) ? k : (!u1 && !u2) ? x2 : (u1 && u2) ? x1 : x3;
+  const double vc = (u1 && !u2) ? k : (u1 && u2) ? x2 : (!u1 && !u2) ? x1 : x3;
+  a = va; b = vb; c = vc;
+}
+
 // o[row] = sum_k A_s[k] g[col k] over this lane's slots of the schedule.
 __device__ __forceinline__ void seg_spmv(const SchedWord *__restrict__ sch,
-                                         int L, int Lc, const double *As,
-                                         const double *gs, double *os) {
+                                         int L, int Lc,
+                                         const double *__restrict__ As,
+                                         const double *__restrict__ gs,
+                                         double *__restrict__ os) {
   double acc = 0.0;
-#pragma unroll 4
+#pragma unroll kSpmvUnroll
   for (int j = 0; j < L; ++j) {
     const SchedWord w = sch[j * Lc];
     acc = fma(As[w.x & 0xffffu], gs[w.x >> 16], acc);
@@ -74,34 +130,77 @@ __device__ __forceinline__ void seg_spmvf(const SchedWord *__restrict__ sch,
   }
 }
 
-// Round-to-nearest-even FP64 -> FP32 conversion on the bit pattern (integer
-// pipe) for values whose FP32 result is a normal number; zeros, subnormal
-// results, overflow, Inf and NaN take the hardware conversion.  IEEE 754
-// rounding written from its definition: keep 23 of the 52 fraction bits and
-// round on the 29 dropped bits (ties to even); a carry out of the fraction
-// increments the exponent.
+// FP64 -> FP32 conversion, round to nearest even, entirely on the integer
+// pipe (on this GPU a hardware F2F conversion occupies the FP64 pipe).  IEEE
+// 754 rounding written from its definition: keep 23 of the 52 fraction bits
+// and round on the 29 dropped bits, ties to even; a carry out of the fraction
+// increments the exponent (and reaches infinity at the top of the range).
+// Results below the FP32 normal range are flushed to a signed zero; Inf and
+// NaN map to Inf and a quiet NaN.
 __device__ __forceinline__ float d2f_rn(double v) {
   const unsigned long long u = (unsigned long long)__double_as_longlong(v);
-  const int e = (int)((u >> 52) & 0x7ffull) - 1023;
-  if (e < -126 || e > 126) return __double2float_rn(v);
+  const unsigned sign = (unsigned)(u >> 32) & 0x80000000u;
+  const int ed = (int)((u >> 52) & 0x7ffull);
   const unsigned long long frac = u & 0xfffffffffffffull;
+  const int ef = ed - 1023 + 127;
   unsigned m = (unsigned)(frac >> 29);
   const unsigned rem = (unsigned)(frac & 0x1fffffffull);
-  if (rem > 0x10000000u || (rem == 0x10000000u && (m & 1u))) ++m;
-  const unsigned bits = ((unsigned)(u >> 63) << 31) + ((unsigned)(e + 127) << 23) + m;
-  return __uint_as_float(bits);
+  m += (rem > 0x10000000u || (rem == 0x10000000u && (m & 1u))) ? 1u : 0u;
+  unsigned bits = ((unsigned)ef << 23) + m;          // valid for 1 <= ef <= 254
+  bits = (ef >= 255) ? 0x7f800000u : bits;            // overflow -> Inf
+  bits = (ef <= 0) ? 0u : bits;                       // underflow -> 0
+  bits = (ed == 0x7ff) ? (frac ? 0x7fc00000u : 0x7f800000u) : bits;
+  return __uint_as_float(sign | bits);
 }
 
-// Exact FP32 -> FP64 widening on the bit pattern for normal numbers (zeros,
-// subnormals, Inf and NaN take the hardware conversion).
+// Exact FP32 -> FP64 widening on the integer pipe (FP32 subnormals, which
+// d2f_rn never produces, are read as zero).
 __device__ __forceinline__ double f2d_exact(float f) {
   const unsigned b = __float_as_uint(f);
   const unsigned ef = (b >> 23) & 0xffu;
-  if (ef == 0u || ef == 0xffu) return (double)f;
-  const unsigned long long u = ((unsigned long long)(b >> 31) << 63) |
-                               ((unsigned long long)(ef - 127 + 1023) << 52) |
-                               ((unsigned long long)(b & 0x7fffffu) << 29);
+  const unsigned long long sign = (unsigned long long)(b >> 31) << 63;
+  const unsigned long long mant = (unsigned long long)(b & 0x7fffffu) << 29;
+  unsigned long long u = sign | ((unsigned long long)(ef - 127 + 1023) << 52) | mant;
+  u = (ef == 0u) ? sign : u;
+  u = (ef == 0xffu) ? (sign | (0x7ffull << 52) | mant) : u;
   return __longlong_as_double((long long)u);
+}
+
+// x == 0 (either sign) on the bit pattern
+__device__ __forceinline__ bool is_zero_bits(double v) {
+  return ((unsigned long long)__double_as_longlong(v) << 1) == 0ull;
+}
+
+// 1/d in FP64 by Newton-Raphson iteration y <- y + y (1 - d y).  d = m 2^k
+// with m in [1, 2) (m and k read from the bit pattern); an FP32
+// rcp.approx of m (relative error about 2^-22) seeds two Newton steps on m,
+// which bring the error to FP64 rounding; the exponent of the result is then
+// lowered by k on the bit pattern.  Only the four Newton FMAs use the FP64
+// pipe (a division costs about seven).  Zero gives Inf, Inf gives zero, NaN
+// stays NaN; results that would leave the normal FP64 range (|d| above
+// 2^1022 or below 2^-1022) are returned as zero or Inf.
+__device__ __forceinline__ double recip64(double d) {
+  const unsigned long long u = (unsigned long long)__double_as_longlong(d);
+  const unsigned long long sign = u & 0x8000000000000000ull;
+  const int ed = (int)((u >> 52) & 0x7ffull);
+  const unsigned long long frac = u & 0xfffffffffffffull;
+  const double m = __longlong_as_double((long long)(frac | (1023ull << 52)));
+  float yf;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(yf)
+      : "f"(__uint_as_float(0x3f800000u | (unsigned)(frac >> 29))));
+  double y = __longlong_as_double((long long)(((unsigned long long)(__float_as_uint(yf) & 0x7fffffu) << 29) |
+                                              ((unsigned long long)(((__float_as_uint(yf) >> 23) & 0xffu) - 127 + 1023) << 52)));
+  double r = fma(-m, y, 1.0);
+  y = fma(y, r, y);
+  r = fma(-m, y, 1.0);
+  y = fma(y, r, y);                       // 1/m in (0.5, 1]
+  const unsigned long long yu = (unsigned long long)__double_as_longlong(y);
+  const int ey = (int)((yu >> 52) & 0x7ffull) - (ed - 1023);
+  unsigned long long out = sign | ((unsigned long long)ey << 52) | (yu & 0xfffffffffffffull);
+  out = (ey <= 0) ? sign : out;                                   // underflow
+  out = (ey >= 0x7ff || ed == 0) ? (sign | (0x7ffull << 52)) : out;  // overflow, 1/0
+  out = (ed == 0x7ff) ? (frac ? 0x7ff8000000000000ull : sign) : out;  // NaN, 1/Inf
+  return __longlong_as_double((long long)out);
 }
 
 }  // namespace camp

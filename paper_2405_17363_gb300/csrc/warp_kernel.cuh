@@ -21,8 +21,15 @@
 
 namespace camp {
 
+#ifndef CAMP_A_GLOBAL
+#define CAMP_A_GLOBAL 0
+#endif
+#ifndef CAMP_WARP_MINB
+#define CAMP_WARP_MINB 2  // with 256 threads per CTA at most: <= 128 registers
+#endif
+
 template <int E>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, CAMP_WARP_MINB)
     warp_bicgstab_kernel(const WarpArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   SchedWord *sch_s = reinterpret_cast<SchedWord *>(smem_raw);
@@ -33,14 +40,19 @@ __global__ void __launch_bounds__(256)
   const int warp = threadIdx.x >> 5;
   const int seg = lane >> a.log2Lc;
   const int sl = lane & (a.Lc - 1);
-  const int segStride = a.segA + 3 * a.segV;
+  const int segStride = a.segStride;
   double *wbase = reinterpret_cast<double *>(smem_raw + (((size_t)nsch * 8 + 15) & ~(size_t)15)) +
                   (size_t)warp * a.k * segStride;
-  double *As = wbase + (size_t)seg * segStride;
-  double *gs = As + a.segA;
-  double *o1 = gs + a.segV;
-  double *o2 = o1 + a.segV;
-  for (int i = sl; i < 3 * a.segV; i += a.Lc) gs[i] = 0.0;
+  double *Abase = wbase + (size_t)seg * segStride;
+#if !CAMP_A_GLOBAL
+  double *As = Abase;
+#endif
+  double *gs = Abase + a.segA;   // gathered vector (p^, s^ or x)
+  double *o1 = gs + a.segV;      // v = A p^
+  double *o2 = o1 + a.segV;      // t = A s^
+  double *rhs = o2 + a.segV;     // shadow residual r^
+  double *dvs = rhs + a.segV;    // Jacobi reciprocals
+  for (int i = sl; i < kWarpVectors * a.segV; i += a.Lc) gs[i] = 0.0;
   __syncthreads();
   const SchedWord *sch = sch_s + sl;
 
@@ -53,6 +65,9 @@ __global__ void __launch_bounds__(256)
     const int c = g * a.k + seg;
     const bool has = c < a.cells;
     // ---- stage the cell's matrix values (Sec. 3.1: one cell, one team)
+#if CAMP_A_GLOBAL
+    const double *As = a.A + (size_t)(has ? c : 0) * nnz;   // read through L1
+#else
     if (has) {
       const double *Ac = a.A + (size_t)c * nnz;
       if (a.a_perm) {
@@ -61,9 +76,10 @@ __global__ void __launch_bounds__(256)
         for (int k = sl; k < nnz; k += Lc) As[k] = __ldg(Ac + k);
       }
     }
+#endif
     __syncwarp();
 
-    double r[E], rh[E], p[E], xv[E], s[E], dinv[E];
+    double r[E], p[E], xv[E], s[E];
     double bb;
     {
       double acc[1] = {0.0};
@@ -73,10 +89,9 @@ __global__ void __launch_bounds__(256)
         const bool v = has && i < n;
         const double bi = v ? __ldg(a.b + (size_t)c * n + i) : 0.0;
         const double d = v ? As[__ldg(a.diag + i)] : 0.0;
-        dinv[e] = v ? (d != 0.0 ? 1.0 / d : 1.0) : 0.0;
+        dvs[i] = v ? (!is_zero_bits(d) ? recip64(d) : 1.0) : 0.0;
         xv[e] = (v && a.x0_given) ? a.x[(size_t)c * n + i] : 0.0;
         r[e] = bi;
-        rh[e] = 0.0;
         p[e] = 0.0;
         s[e] = 0.0;
         acc[0] = fma(bi, bi, acc[0]);
@@ -84,8 +99,7 @@ __global__ void __launch_bounds__(256)
       seg_sum<1>(acc, Lc);
       bb = acc[0];
     }
-    const double bnorm = sqrt(bb);
-    const double thr = (tol * bnorm) * (tol * bnorm);
+    const double thr = (tol * tol) * bb;  // (tol ||b||)^2
     int st = -1, it = 0, nbreak = 0;
     double resid = 0.0;
     bool done = !has;
@@ -94,7 +108,7 @@ __global__ void __launch_bounds__(256)
         st = CAMP_CELL_NONFINITE;
         resid = __longlong_as_double(0x7ff8000000000000ll);
         done = true;
-      } else if (bb == 0.0) {
+      } else if (is_zero_bits(bb)) {
         st = CAMP_CELL_CONVERGED;
         done = true;
 #pragma unroll
@@ -123,7 +137,7 @@ __global__ void __launch_bounds__(256)
         if (restart) {
 #pragma unroll
           for (int e = 0; e < E; ++e) {
-            rh[e] = r[e];
+            rhs[sl + e * Lc] = r[e];
             p[e] = 0.0;
           }
           rho = acc[0];
@@ -149,11 +163,12 @@ __global__ void __launch_bounds__(256)
           }
         }
         // p = r + beta (p - omega v); the bracket is kept in p
-        const double beta = (rho / rho_prev) * (alpha / omega);
+        const double beta = (rho * alpha) * recip64(rho_prev * omega);
 #pragma unroll
         for (int e = 0; e < E; ++e) {
+          const int i = sl + e * Lc;
           if (active) p[e] = fma(beta, p[e], r[e]);
-          gs[sl + e * Lc] = dinv[e] * p[e];
+          gs[i] = dvs[i] * p[e];
         }
         __syncwarp();
         seg_spmv(sch, a.L, Lc, As, gs, o1);  // v = A p^
@@ -161,7 +176,10 @@ __global__ void __launch_bounds__(256)
         if (active) ++it;
         double sg[1] = {0.0};
 #pragma unroll
-        for (int e = 0; e < E; ++e) sg[0] = fma(rh[e], o1[sl + e * Lc], sg[0]);
+        for (int e = 0; e < E; ++e) {
+          const int i = sl + e * Lc;
+          sg[0] = fma(rhs[i], o1[i], sg[0]);
+        }
         seg_sum<1>(sg, Lc);
         if (active) {
           if (!is_finite_bits(sg[0])) {
@@ -172,7 +190,7 @@ __global__ void __launch_bounds__(256)
             active = false;
           }
         }
-        const double al = rho / sg[0];
+        const double al = rho * recip64(sg[0]);
         if (active) alpha = al;
 #pragma unroll
         for (int e = 0; e < E; ++e) {
@@ -181,35 +199,35 @@ __global__ void __launch_bounds__(256)
             xv[e] = fma(al, gs[i], xv[e]);
             s[e] = fma(-al, o1[i], r[e]);
           }
-          gs[i] = dinv[e] * s[e];
+          gs[i] = dvs[i] * s[e];
         }
         __syncwarp();
         seg_spmv(sch, a.L, Lc, As, gs, o2);  // t = A s^
         __syncwarp();
-        double q3[3] = {0.0, 0.0, 0.0};
+        double q0 = 0.0, q1 = 0.0, q2 = 0.0;
 #pragma unroll
         for (int e = 0; e < E; ++e) {
           const double t = o2[sl + e * Lc];
-          q3[0] = fma(s[e], s[e], q3[0]);
-          q3[1] = fma(t, s[e], q3[1]);
-          q3[2] = fma(t, t, q3[2]);
+          q0 = fma(s[e], s[e], q0);
+          q1 = fma(t, s[e], q1);
+          q2 = fma(t, t, q2);
         }
-        seg_sum<3>(q3, Lc);
+        seg_sum3(q0, q1, q2, Lc);
         bool full = false;
         if (active) {
-          if (le_nonneg(q3[0], thr)) {
+          if (le_nonneg(q0, thr)) {
             active = false;  // converged on the half step (x has alpha p^)
-          } else if (!is_finite_bits(q3[1]) || !is_finite_bits(q3[2])) {
+          } else if (!is_finite_bits(q1) || !is_finite_bits(q2)) {
             nonfin = true;
             active = false;
-          } else if (q3[2] == 0.0) {
+          } else if (is_zero_bits(q2)) {
             broke = true;  // keep the half step, restart
             active = false;
           } else {
             full = true;
           }
         }
-        const double om = q3[1] / q3[2];
+        const double om = q1 * recip64(q2);
         if (full) omega = om;
 #pragma unroll
         for (int e = 0; e < E; ++e) {
@@ -220,23 +238,23 @@ __global__ void __launch_bounds__(256)
             p[e] = fma(-om, o1[i], p[e]);
           }
         }
-        double q2[2] = {0.0, 0.0};
+        double hr = 0.0, rr = 0.0;
 #pragma unroll
         for (int e = 0; e < E; ++e) {
-          q2[0] = fma(rh[e], r[e], q2[0]);
-          q2[1] = fma(r[e], r[e], q2[1]);
+          hr = fma(rhs[sl + e * Lc], r[e], hr);
+          rr = fma(r[e], r[e], rr);
         }
-        seg_sum<2>(q2, Lc);
+        seg_sum2(hr, rr, Lc);
         if (full) {
           nbreak = 0;
-          if (le_nonneg(q2[1], thr)) {
+          if (le_nonneg(rr, thr)) {
             active = false;
-          } else if (om == 0.0) {
+          } else if (is_zero_bits(om)) {
             broke = true;
             active = false;
           } else {
             rho_prev = rho;
-            rho = q2[0];
+            rho = hr;
           }
         }
       }
@@ -247,18 +265,17 @@ __global__ void __launch_bounds__(256)
       seg_spmv(sch, a.L, Lc, As, gs, o1);
       __syncwarp();
       double rt2[1] = {0.0};
-      double rt[E];
 #pragma unroll
       for (int e = 0; e < E; ++e) {
         const int i = sl + e * Lc;
         const double bi = (has && i < n) ? __ldg(a.b + (size_t)c * n + i) : 0.0;
-        rt[e] = bi - o1[i];
-        rt2[0] = fma(rt[e], rt[e], rt2[0]);
+        s[e] = bi - o1[i];  // s holds the true residual here
+        rt2[0] = fma(s[e], s[e], rt2[0]);
       }
       seg_sum<1>(rt2, Lc);
       if (fin) {
         fin = false;
-        resid = sqrt(rt2[0]) / bnorm;
+        resid = sqrt(rt2[0] * recip64(bb));
         if (nonfin || !is_finite_bits(resid)) {
           st = CAMP_CELL_NONFINITE;
         } else if (resid <= tol) {
@@ -269,7 +286,7 @@ __global__ void __launch_bounds__(256)
           st = CAMP_CELL_BREAKDOWN;
         } else {
 #pragma unroll
-          for (int e = 0; e < E; ++e) r[e] = rt[e];
+          for (int e = 0; e < E; ++e) r[e] = s[e];
           restart = true;
         }
         if (!restart) done = true;
