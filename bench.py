@@ -224,6 +224,37 @@ def time_e2e(camp, solver, cb, C, tol, maxit, steps, world, dev):
             "d2h_bytes_per_step": C * (m.n * 8 + 4 + 8 + 4)}
 
 
+def time_uneven(camp, dev, flush, stream, steps=50):
+    """The uneven-batching workload (40/90 x 20000 + 80/200 x 5000 + 150/400 x
+    500 cells, gamma up to 1): one persistent launch under a CUDA graph against
+    three plain FP64 launches back to back, both to the 1e-10 true residual."""
+    import torch
+    cbs, tol, maxit = synth.workload(2)
+    solvers = [camp.Solver(cb.mech.row_ptr, cb.mech.col_idx) for cb in cbs]
+    A = [torch.as_tensor(cb.A_vals, device=dev) for cb in cbs]
+    b = [torch.as_tensor(cb.b, device=dev) for cb in cbs]
+    batch = camp.Batch(solvers)
+    out = batch.solve(A, b, tol, maxit)
+    t_batch = time_steps(lambda: batch.solve(A, b, tol, maxit, out=out), flush, stream, steps, 3)
+    outs = [sv.solve(a, v, tol, maxit) for sv, a, v in zip(solvers, A, b)]
+
+    def plain():
+        for sv, a, v, o in zip(solvers, A, b, outs):
+            sv.solve(a, v, tol, maxit, out=o)
+    t_plain = time_steps(plain, flush, stream, steps, 3)
+    cells = sum(cb.cells for cb in cbs)
+    mb, mp = sum(t_batch) / steps, sum(t_plain) / steps
+    conv = sum(int((o[3] == 0).sum().item()) for o in out)
+    iters = np.concatenate([o[1].cpu().numpy() for o in out])
+    batch.close()
+    for sv in solvers:
+        sv.close()
+    return {"workload": synth.WORKLOADS[2][0], "cells": cells,
+            "persistent_graph": {"ms_per_step": mb, "value": cells / (mb * 1e-3), "unit": UNIT},
+            "three_plain_launches": {"ms_per_step": mp, "value": cells / (mp * 1e-3), "unit": UNIT},
+            "converged": conv, "iters_mean": float(iters.mean()), "iters_max": int(iters.max())}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -308,6 +339,7 @@ def main():
 
     mixed_side = None
     e2e = None
+    uneven = None
     if not args.skip_extras:
         if args.mode == "fp64":
             mt = time_steps(solve_mixed, flush, stream, 200, 5)
@@ -321,6 +353,7 @@ def main():
                 "converged": int((st == 0).sum().item()),
                 "speedup_vs_fp64": ms_step / mms}
         e2e = time_e2e(camp, solver, cb, C, tol, maxit, args.e2e_steps, world, dev)
+        uneven = time_uneven(camp, dev, flush, stream) if rank == 0 else None
 
     if rank == 0:
         cpu = cpu_baseline(m, cb.A_vals, cb.b, tol, maxit, args.cpu_seconds) \
@@ -354,6 +387,8 @@ def main():
             line["roofline"] = None
         if mixed_side is not None:
             line["mixed_fp32_inner"] = mixed_side
+        if uneven is not None:
+            line["uneven_batch"] = uneven
         if cpu is not None:
             line["cpu_baseline"] = cpu
         print(json.dumps(line), flush=True)

@@ -44,6 +44,7 @@ extern "C" {
 #endif
 
 typedef struct camp_solver *camp_solver_t;
+typedef struct camp_batch *camp_batch_t;
 
 typedef enum {
   CAMP_OK = 0,
@@ -171,6 +172,44 @@ camp_status camp_solver_solve_mixed(camp_solver_t h, int cells,
                                     double tol_inner, int maxit_inner,
                                     int *iters_out, int *sweeps_out,
                                     double *resid_out, int *status_out);
+
+/*
+ * Uneven batching: one persistent launch solves the cells of up to 8
+ * mechanisms (patterns of different sizes) together.  Each warp takes work
+ * items -- one group of 32/lanes cells of one mechanism -- from a device
+ * queue head (an atomic counter, reset by the same CUDA graph that launches
+ * the kernel) until the queue is empty; mechanisms with more species are
+ * queued first.  The solve of every cell is the one of camp_solver_solve.
+ * mechs [nmech] are existing solver handles (not owned; they must outlive the
+ * batch).  Allocates the 4-byte queue head on the device.
+ */
+camp_status camp_batch_create(camp_batch_t *out, int nmech,
+                              const camp_solver_t *mechs);
+camp_status camp_batch_destroy(camp_batch_t b);
+camp_status camp_batch_set_stream(camp_batch_t b, void *stream);
+
+/*
+ * Launch configuration of the batch (the autotuner's knobs; 0 = automatic):
+ * rows_per_lane in {3, 4, 5, 6, 8} fixes the lanes per cell of every
+ * mechanism (fewest lanes with at most that many rows per lane), so the cells
+ * per warp; warps_per_block in [1, 8]; stage_A_in_smem = 1 copies each cell's
+ * matrix values to shared memory, 0 reads them through L1.
+ */
+camp_status camp_batch_set_config(camp_batch_t b, int rows_per_lane,
+                                  int warps_per_block, int stage_A_in_smem);
+
+/*
+ * Solve cells[m] cells of every mechanism m in one launch (captured once in a
+ * CUDA graph and replayed; a change of launch shape re-captures it).  The
+ * arrays are HOST arrays [nmech] of DEVICE pointers with the layouts of
+ * camp_solver_solve; status_out may be NULL (or hold NULL entries).
+ * Asynchronous on the batch's stream.
+ */
+camp_status camp_batch_solve(camp_batch_t b, const int *cells,
+                             const double *const *A_vals,
+                             const double *const *bvec, double *const *x,
+                             double tol, int maxit, int *const *iters_out,
+                             double *const *resid_out, int *const *status_out);
 
 /*
  * Inspect the static SpMV schedule the warp-packed kernels use for a pattern

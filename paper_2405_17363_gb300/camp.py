@@ -51,6 +51,11 @@ _grad_A = _sig("camp_solver_grad_A", [_P, _I, _P, _P, _P])
 _solve_host = _sig("camp_solver_solve_host", [_P, _I, _P, _P, _P, _D, _I, _P, _P, _P])
 _solve_mixed = _sig("camp_solver_solve_mixed",
                     [_P, _I, _P, _P, _P, _D, _I, _D, _I, _P, _P, _P, _P])
+_batch_create = _sig("camp_batch_create", [ctypes.POINTER(_P), _I, _P])
+_batch_destroy = _sig("camp_batch_destroy", [_P])
+_batch_set_stream = _sig("camp_batch_set_stream", [_P, _P])
+_batch_set_config = _sig("camp_batch_set_config", [_P, _I, _I, _I])
+_batch_solve = _sig("camp_batch_solve", [_P, _P, _P, _P, _P, _D, _I, _P, _P, _P])
 _last_error = _sig("camp_last_error", [], ctypes.c_char_p)
 _version = _sig("camp_version", [], ctypes.c_char_p)
 
@@ -184,6 +189,42 @@ def camp_solver_solve_mixed(h, cells, A_vals, b, x, tol, max_sweeps, tol_inner,
            "camp_solver_solve_mixed")
 
 
+def camp_batch_create(solver_handles) -> int:
+    arr = (_P * len(solver_handles))(*solver_handles)
+    h = _P()
+    _check(_batch_create(ctypes.byref(h), len(solver_handles), arr), "camp_batch_create")
+    return h.value
+
+
+def camp_batch_destroy(h: int):
+    _check(_batch_destroy(h), "camp_batch_destroy")
+
+
+def camp_batch_set_config(h: int, rows_per_lane=0, warps_per_block=0, stage_A_in_smem=1):
+    _check(_batch_set_config(h, rows_per_lane, warps_per_block, stage_A_in_smem),
+           "camp_batch_set_config")
+
+
+def camp_batch_solve(h, cells, A_vals, b, x, tol, maxit, iters_out, resid_out,
+                     status_out=None):
+    """cells: list of ints; the other arguments are lists of CUDA tensors
+    (one per mechanism)."""
+    nm = len(cells)
+    s = torch.cuda.current_stream()
+    _check(_batch_set_stream(h, s.cuda_stream), "camp_batch_set_stream")
+
+    def arr(ts, dtype, name):
+        return (_P * nm)(*[_dptr(t, dtype, name) if t is not None else None for t in ts])
+
+    c_cells = (_I * nm)(*[int(c) for c in cells])
+    st = arr(status_out, torch.int32, "status_out") if status_out is not None else None
+    _check(_batch_solve(h, c_cells, arr(A_vals, torch.float64, "A_vals"),
+                        arr(b, torch.float64, "b"), arr(x, torch.float64, "x"),
+                        float(tol), int(maxit), arr(iters_out, torch.int32, "iters_out"),
+                        arr(resid_out, torch.float64, "resid_out"), st),
+           "camp_batch_solve")
+
+
 # ---- convenience wrapper ------------------------------------------------
 
 class Solver:
@@ -248,6 +289,43 @@ class Solver:
         camp_solver_solve_mixed(self.h, cells, A_vals, b, x, tol, max_sweeps, tol_inner,
                                 maxit_inner, iters, sweeps, resid, status)
         return x, iters, sweeps, resid, status
+
+
+class Batch:
+    """Several mechanisms solved by one persistent launch (uneven batching)."""
+
+    def __init__(self, solvers):
+        self.solvers = list(solvers)
+        self.h = camp_batch_create([sv.h for sv in self.solvers])
+
+    def close(self):
+        if getattr(self, "h", None):
+            camp_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_config(self, rows_per_lane=0, warps_per_block=0, stage_A_in_smem=1):
+        camp_batch_set_config(self.h, rows_per_lane, warps_per_block, stage_A_in_smem)
+
+    def solve(self, A_list, b_list, tol=1e-10, maxit=500, out=None):
+        """Returns a list of (x, iters, resid, status), one per mechanism."""
+        if out is None:
+            out = []
+            for sv, b in zip(self.solvers, b_list):
+                c = b.shape[0]
+                out.append((torch.empty((c, sv.n), dtype=torch.float64, device=b.device),
+                            torch.empty(c, dtype=torch.int32, device=b.device),
+                            torch.empty(c, dtype=torch.float64, device=b.device),
+                            torch.empty(c, dtype=torch.int32, device=b.device)))
+        camp_batch_solve(self.h, [b.shape[0] for b in b_list], A_list, b_list,
+                         [o[0] for o in out], tol, maxit, [o[1] for o in out],
+                         [o[2] for o in out], [o[3] for o in out])
+        return out
 
 
 class CampSolve(torch.autograd.Function):

@@ -37,6 +37,19 @@ struct WarpArgs {
   int x0_given;
 };
 
+// Persistent launch over up to kMaxMech mechanisms: mechanism m owns work
+// items [item_begin[m], item_begin[m+1]) (one item = one group of
+// 32/m[m].Lc cells); counter is the queue head (reset to 0 before launch).
+constexpr int kMaxMech = 8;
+struct BatchArgs {
+  int nmech;
+  int total_items;
+  int item_begin[kMaxMech + 1];
+  int warp_doubles;            // shared-memory doubles per warp
+  unsigned int *counter;
+  WarpArgs m[kMaxMech];        // schedules in global memory
+};
+
 // Arguments of the block kernel (the paper's Block-cells(k) arrangement):
 // cpb cells per CTA, one thread per row, rows of cell j at threads [j*n, j*n+n).
 struct BlockArgs {
@@ -68,6 +81,10 @@ cudaError_t launch_warp(int E, const WarpArgs &a, int warps_per_block,
                         int grid, size_t smem, cudaStream_t st);
 cudaError_t warp_set_smem(int E, size_t smem);
 cudaError_t warp_occupancy(int E, int warps_per_block, size_t smem, int *blocks);
+// persistent batch kernel: E in {3,4,5,6,8}, A staged in shared memory or not
+const void *batch_kernel(int E, bool a_smem);
+cudaError_t batch_prepare(int E, bool a_smem, int warps_per_block, size_t smem,
+                          int *blocks_per_sm);
 cudaError_t launch_block(const BlockArgs &a, int threads, size_t smem,
                          cudaStream_t st);
 cudaError_t block_set_smem(size_t smem);

@@ -658,4 +658,206 @@ camp_status camp_solver_solve_mixed(camp_solver_t h, int cells,
   return CAMP_OK;
 }
 
+
+// ---- persistent multi-mechanism batch ------------------------------------
+
+struct camp_batch {
+  int device = 0, sms = 0;
+  size_t smem_optin = 0;
+  int nmech = 0;
+  camp_solver *mech[kMaxMech] = {};
+  cudaStream_t stream = nullptr;
+  int E = 0, wpb = 0, a_smem = 1;   // 0 = automatic
+  unsigned int *d_counter = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  cudaGraphNode_t knode = nullptr;
+  int g_E = 0, g_wpb = 0, g_asmem = -1, g_grid = 0;
+  size_t g_smem = 0;
+};
+
+static void batch_drop_graph(camp_batch *b) {
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  b->exec = nullptr;
+  b->graph = nullptr;
+  b->knode = nullptr;
+  b->g_asmem = -1;
+}
+
+camp_status camp_batch_create(camp_batch_t *out, int nmech,
+                              const camp_solver_t *mechs) {
+  if (!out) return fail(CAMP_EINVAL, "null output handle pointer");
+  *out = nullptr;
+  if (nmech < 1 || nmech > kMaxMech)
+    return fail(CAMP_EINVAL, "nmech=%d outside [1, %d]", nmech, kMaxMech);
+  if (!mechs) return fail(CAMP_EINVAL, "null mechanism array");
+  for (int m = 0; m < nmech; ++m)
+    if (!mechs[m]) return fail(CAMP_EINVAL, "null solver handle for mechanism %d", m);
+  camp_batch *b = new (std::nothrow) camp_batch();
+  if (!b) return fail(CAMP_ENOMEM, "host allocation failed");
+  b->nmech = nmech;
+  for (int m = 0; m < nmech; ++m) b->mech[m] = mechs[m];
+  b->device = mechs[0]->device;
+  b->sms = mechs[0]->sms;
+  b->smem_optin = mechs[0]->smem_optin;
+  cudaError_t e = cudaSetDevice(b->device);
+  if (e == cudaSuccess) e = cudaMalloc(&b->d_counter, sizeof(unsigned int));
+  if (e != cudaSuccess) {
+    delete b;
+    return cuda_fail(e, "batch create");
+  }
+  *out = b;
+  return CAMP_OK;
+}
+
+camp_status camp_batch_destroy(camp_batch_t b) {
+  if (!b) return CAMP_OK;
+  cudaSetDevice(b->device);
+  cudaStreamSynchronize(b->stream);
+  batch_drop_graph(b);
+  cudaFree(b->d_counter);
+  delete b;
+  return CAMP_OK;
+}
+
+camp_status camp_batch_set_stream(camp_batch_t b, void *stream) {
+  if (!b) return fail(CAMP_EINVAL, "null batch handle");
+  b->stream = (cudaStream_t)stream;
+  return CAMP_OK;
+}
+
+camp_status camp_batch_set_config(camp_batch_t b, int rows_per_lane,
+                                  int warps_per_block, int stage_A_in_smem) {
+  if (!b) return fail(CAMP_EINVAL, "null batch handle");
+  if (rows_per_lane != 0 && rows_per_lane != 3 && rows_per_lane != 4 &&
+      rows_per_lane != 5 && rows_per_lane != 6 && rows_per_lane != 8)
+    return fail(CAMP_EINVAL, "rows_per_lane must be 0 (auto), 3, 4, 5, 6 or 8");
+  if (warps_per_block < 0 || warps_per_block > 8)
+    return fail(CAMP_EINVAL, "warps_per_block must be in [0, 8]");
+  b->E = rows_per_lane;
+  b->wpb = warps_per_block;
+  b->a_smem = stage_A_in_smem ? 1 : 0;
+  return CAMP_OK;
+}
+
+camp_status camp_batch_solve(camp_batch_t b, const int *cells,
+                             const double *const *A_vals,
+                             const double *const *bvec, double *const *x,
+                             double tol, int maxit, int *const *iters_out,
+                             double *const *resid_out, int *const *status_out) {
+  if (!b) return fail(CAMP_EINVAL, "null batch handle");
+  if (!cells || !A_vals || !bvec || !x || !iters_out || !resid_out)
+    return fail(CAMP_EINVAL, "null argument array");
+  if (!(tol > 0.0) || !std::isfinite(tol)) return fail(CAMP_EINVAL, "tol must be finite and > 0");
+  if (maxit < 1) return fail(CAMP_EINVAL, "maxit must be >= 1");
+  int max_n = 0;
+  for (int m = 0; m < b->nmech; ++m) {
+    if (cells[m] < 0) return fail(CAMP_EINVAL, "cells[%d] < 0", m);
+    if (cells[m] > 0 && (!A_vals[m] || !bvec[m] || !x[m] || !iters_out[m] || !resid_out[m]))
+      return fail(CAMP_EINVAL, "null array pointer for mechanism %d", m);
+    max_n = std::max(max_n, b->mech[m]->n);
+  }
+  cudaError_t e = cudaSetDevice(b->device);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
+  // rows per lane shared by all mechanisms (one kernel instantiation)
+  static const int kEs[] = {3, 4, 5, 6, 8};
+  int E = b->E;
+  if (E == 0) {
+    E = 5;
+    while ((max_n + 31) / 32 > E) E = (E == 5) ? 6 : 8;
+  }
+  if ((max_n + 31) / 32 > E)
+    return fail(CAMP_EUNSUPPORTED, "n=%d needs more than %d rows per lane", max_n, E);
+  (void)kEs;
+  const bool asmem = b->a_smem != 0;
+  // queue order: mechanisms with more species first
+  int order[kMaxMech];
+  for (int m = 0; m < b->nmech; ++m) order[m] = m;
+  std::stable_sort(order, order + b->nmech,
+                   [&](int p, int q) { return b->mech[p]->n > b->mech[q]->n; });
+  BatchArgs args;
+  memset(&args, 0, sizeof args);
+  args.nmech = b->nmech;
+  args.counter = b->d_counter;
+  int items = 0, warp_doubles = 0;
+  for (int q = 0; q < b->nmech; ++q) {
+    const int m = order[q];
+    camp_solver *h = b->mech[m];
+    View &v = h->fwd;
+    int Lc = 1;
+    while ((v.n + Lc - 1) / Lc > E) Lc *= 2;
+    Schedule *S = nullptr;
+    if ((e = view_schedule(v, Lc, &S)) != cudaSuccess) return cuda_fail(e, "schedule upload");
+    WarpArgs &a = args.m[q];
+    a.cells = cells[m]; a.n = v.n; a.nnz = v.nnz;
+    a.Lc = Lc; a.log2Lc = ilog2(Lc); a.k = 32 / Lc; a.L = S->L;
+    a.segA = asmem ? ((v.nnz + 1) & ~1) : 0;
+    a.segV = ((E * Lc + 1) + 1) & ~1;
+    a.segStride = bank_spread_stride(a.segA + kWarpVectors * a.segV, a.k);
+    a.ngroups = (cells[m] + a.k - 1) / a.k;
+    a.A = A_vals[m]; a.b = bvec[m]; a.x = x[m]; a.iters = iters_out[m];
+    a.resid = resid_out[m]; a.status = status_out ? status_out[m] : nullptr;
+    a.a_perm = nullptr; a.diag = v.d_diag; a.sched = S->d_words;
+    a.tol = tol; a.maxit = maxit; a.x0_given = 0;
+    args.item_begin[q] = items;
+    items += a.ngroups;
+    warp_doubles = std::max(warp_doubles, a.k * a.segStride);
+  }
+  args.item_begin[b->nmech] = items;
+  args.total_items = items;
+  args.warp_doubles = warp_doubles;
+  if (items == 0) return CAMP_OK;
+  int wpb = b->wpb > 0 ? b->wpb : 4;
+  size_t smem = (size_t)wpb * warp_doubles * 8;
+  while (smem > b->smem_optin && wpb > 1) smem = (size_t)(--wpb) * warp_doubles * 8;
+  if (smem > b->smem_optin) return fail(CAMP_EUNSUPPORTED, "a warp's cells do not fit in shared memory");
+  int occ = 0;
+  if ((e = batch_prepare(E, asmem, wpb, smem, &occ)) != cudaSuccess) return cuda_fail(e, "batch occupancy");
+  if (occ < 1) occ = 1;
+  const int grid = std::max(1, std::min(b->sms * occ, (items + wpb - 1) / wpb));
+  void *kparams[] = {&args};
+  if (!b->exec || b->g_E != E || b->g_wpb != wpb || b->g_asmem != (int)asmem ||
+      b->g_grid != grid || b->g_smem != smem) {
+    batch_drop_graph(b);
+    cudaGraphNode_t mnode;
+    cudaMemsetParams mp;
+    memset(&mp, 0, sizeof mp);
+    mp.dst = b->d_counter;
+    mp.value = 0;
+    mp.elementSize = sizeof(unsigned int);
+    mp.width = 1;
+    mp.height = 1;
+    mp.pitch = sizeof(unsigned int);
+    cudaKernelNodeParams kp;
+    memset(&kp, 0, sizeof kp);
+    kp.func = const_cast<void *>(batch_kernel(E, asmem));
+    kp.gridDim = dim3(grid);
+    kp.blockDim = dim3(wpb * 32);
+    kp.sharedMemBytes = (unsigned)smem;
+    kp.kernelParams = kparams;
+    if ((e = cudaGraphCreate(&b->graph, 0)) != cudaSuccess ||
+        (e = cudaGraphAddMemsetNode(&mnode, b->graph, nullptr, 0, &mp)) != cudaSuccess ||
+        (e = cudaGraphAddKernelNode(&b->knode, b->graph, &mnode, 1, &kp)) != cudaSuccess ||
+        (e = cudaGraphInstantiate(&b->exec, b->graph, 0)) != cudaSuccess) {
+      batch_drop_graph(b);
+      return cuda_fail(e, "batch graph build");
+    }
+    b->g_E = E; b->g_wpb = wpb; b->g_asmem = asmem; b->g_grid = grid; b->g_smem = smem;
+  } else {
+    cudaKernelNodeParams kp;
+    memset(&kp, 0, sizeof kp);
+    kp.func = const_cast<void *>(batch_kernel(E, asmem));
+    kp.gridDim = dim3(grid);
+    kp.blockDim = dim3(wpb * 32);
+    kp.sharedMemBytes = (unsigned)smem;
+    kp.kernelParams = kparams;
+    if ((e = cudaGraphExecKernelNodeSetParams(b->exec, b->knode, &kp)) != cudaSuccess)
+      return cuda_fail(e, "batch graph update");
+  }
+  if ((e = cudaGraphLaunch(b->exec, b->stream)) != cudaSuccess)
+    return cuda_fail(e, "batch graph launch");
+  return CAMP_OK;
+}
+
 }  // extern "C"

@@ -8,9 +8,12 @@
 // per-cell scalars (rho, alpha, omega, ...) are replicated in the segment's
 // lanes; every FP64 instruction is issued once for all k cells of the warp.
 //
-// Shared memory per CTA: the SpMV schedule (shared by all warps), then per
-// cell: its matrix values A_s [segA], the gathered vector g_s [segV] and the
-// two product vectors o1_s = A p^, o2_s = A s^ [segV each].
+// Shared memory per cell: its matrix values A_s [segA] (unless read through
+// L1 from global memory), the gathered vector g_s, the products o1_s = A p^
+// and o2_s = A s^, the shadow residual and the Jacobi reciprocals [segV each].
+// The plain launch also keeps the SpMV schedule in shared memory; the
+// persistent launch (several mechanisms) reads each mechanism's schedule
+// through L1.
 //
 // The iteration is right-preconditioned BiCGSTAB with M = diag(A); see the
 // header of the oracle for the readings of the paper (relative 2-norm test on
@@ -21,13 +24,283 @@
 
 namespace camp {
 
-#ifndef CAMP_A_GLOBAL
-#define CAMP_A_GLOBAL 0
-#endif
 #ifndef CAMP_WARP_MINB
 #define CAMP_WARP_MINB 2  // with 256 threads per CTA at most: <= 128 registers
 #endif
 
+// Solve the k = 32/Lc cells of group g (cells g*k .. g*k+k-1) of one
+// mechanism with this warp.  wbase: the warp's shared-memory region; sch: this
+// lane's column of the SpMV schedule (shared or global memory).
+template <int E, bool ASMEM>
+__device__ __forceinline__ void solve_group(const WarpArgs &a, int g,
+                                            double *wbase,
+                                            const SchedWord *sch) {
+  const int lane = threadIdx.x & 31;
+  const int seg = lane >> a.log2Lc;
+  const int sl = lane & (a.Lc - 1);
+  const int n = a.n, nnz = a.nnz, Lc = a.Lc;
+  const double tol = a.tol;
+  double *Abase = wbase + (size_t)seg * a.segStride;
+  double *gs = Abase + a.segA;   // gathered vector (p^, s^ or x)
+  double *o1 = gs + a.segV;      // v = A p^
+  double *o2 = o1 + a.segV;      // t = A s^
+  double *rhs = o2 + a.segV;     // shadow residual r^
+  double *dvs = rhs + a.segV;    // Jacobi reciprocals
+  const int c = g * a.k + seg;
+  const bool has = c < a.cells;
+  // ---- stage the cell's matrix values (Sec. 3.1: one cell, one team)
+  const double *As;
+  if (ASMEM) {
+    if (has) {
+      const double *Ac = a.A + (size_t)c * nnz;
+      if (a.a_perm) {
+        for (int k = sl; k < nnz; k += Lc) Abase[k] = __ldg(Ac + __ldg(a.a_perm + k));
+      } else {
+        for (int k = sl; k < nnz; k += Lc) Abase[k] = __ldg(Ac + k);
+      }
+    }
+    As = Abase;
+  } else {
+    As = a.A + (size_t)(has ? c : 0) * nnz;   // read through L1
+  }
+  // pad rows of the product vectors are never written by the SpMV
+  for (int i = n + sl; i < E * Lc; i += Lc) {
+    o1[i] = 0.0;
+    o2[i] = 0.0;
+  }
+  __syncwarp();
+
+  double r[E], p[E], xv[E], s[E];
+  double bb;
+  {
+    double acc[1] = {0.0};
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+      const int i = sl + e * Lc;
+      const bool v = has && i < n;
+      const double bi = v ? __ldg(a.b + (size_t)c * n + i) : 0.0;
+      const double d = v ? As[__ldg(a.diag + i)] : 0.0;
+      dvs[i] = v ? (!is_zero_bits(d) ? recip64(d) : 1.0) : 0.0;
+      xv[e] = (v && a.x0_given) ? a.x[(size_t)c * n + i] : 0.0;
+      r[e] = bi;
+      p[e] = 0.0;
+      s[e] = 0.0;
+      acc[0] = fma(bi, bi, acc[0]);
+    }
+    seg_sum<1>(acc, Lc);
+    bb = acc[0];
+  }
+  const double thr = (tol * tol) * bb;  // (tol ||b||)^2
+  int st = -1, it = 0, nbreak = 0;
+  double resid = 0.0;
+  bool done = !has;
+  if (has) {
+    if (!is_finite_bits(bb)) {
+      st = CAMP_CELL_NONFINITE;
+      resid = __longlong_as_double(0x7ff8000000000000ll);
+      done = true;
+    } else if (is_zero_bits(bb)) {
+      st = CAMP_CELL_CONVERGED;
+      done = true;
+#pragma unroll
+      for (int e = 0; e < E; ++e) xv[e] = 0.0;
+    }
+  }
+  if (a.x0_given) {  // r = b - A x0
+#pragma unroll
+    for (int e = 0; e < E; ++e) gs[sl + e * Lc] = xv[e];
+    __syncwarp();
+    seg_spmv(sch, a.L, Lc, As, gs, o1);
+    __syncwarp();
+#pragma unroll
+    for (int e = 0; e < E; ++e) r[e] -= o1[sl + e * Lc];
+  }
+
+  bool restart = !done, first = true;
+  bool fin = false, active = false, broke = false, nonfin = false;
+  double rho = 1.0, rho_prev = 1.0, alpha = 1.0, omega = 1.0;
+  for (;;) {
+    {  // (re)start from the current residual r
+      double acc[1] = {0.0};
+#pragma unroll
+      for (int e = 0; e < E; ++e) acc[0] = fma(r[e], r[e], acc[0]);
+      seg_sum<1>(acc, Lc);
+      if (restart) {
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+          rhs[sl + e * Lc] = r[e];
+          p[e] = 0.0;
+        }
+        rho = acc[0];
+        rho_prev = alpha = omega = 1.0;
+        broke = nonfin = false;
+        fin = true;
+        // a restart follows a failed true-residual test: always iterate
+        active = first ? !le_nonneg(acc[0], thr) : true;
+        restart = false;
+        first = false;
+      }
+    }
+    while (__any_sync(kFull, active)) {
+      if (active) {
+        if (it >= a.maxit) {
+          active = false;
+        } else if (!is_finite_bits(rho)) {
+          nonfin = true;
+          active = false;
+        } else if (abs_tiny(rho)) {
+          broke = true;
+          active = false;
+        }
+      }
+      // p = r + beta (p - omega v); the bracket is kept in p
+      const double beta = (rho * alpha) * recip64(rho_prev * omega);
+#pragma unroll
+      for (int e = 0; e < E; ++e) {
+        const int i = sl + e * Lc;
+        if (active) p[e] = fma(beta, p[e], r[e]);
+        gs[i] = dvs[i] * p[e];
+      }
+      __syncwarp();
+      seg_spmv(sch, a.L, Lc, As, gs, o1);  // v = A p^
+      __syncwarp();
+      if (active) ++it;
+      double sg[1] = {0.0};
+#pragma unroll
+      for (int e = 0; e < E; ++e) {
+        const int i = sl + e * Lc;
+        sg[0] = fma(rhs[i], o1[i], sg[0]);
+      }
+      seg_sum<1>(sg, Lc);
+      if (active) {
+        if (!is_finite_bits(sg[0])) {
+          nonfin = true;
+          active = false;
+        } else if (abs_tiny(sg[0])) {
+          broke = true;
+          active = false;
+        }
+      }
+      const double al = rho * recip64(sg[0]);
+      if (active) alpha = al;
+#pragma unroll
+      for (int e = 0; e < E; ++e) {
+        const int i = sl + e * Lc;
+        if (active) {
+          xv[e] = fma(al, gs[i], xv[e]);
+          s[e] = fma(-al, o1[i], r[e]);
+        }
+        gs[i] = dvs[i] * s[e];
+      }
+      __syncwarp();
+      seg_spmv(sch, a.L, Lc, As, gs, o2);  // t = A s^
+      __syncwarp();
+      double q0 = 0.0, q1 = 0.0, q2 = 0.0;
+#pragma unroll
+      for (int e = 0; e < E; ++e) {
+        const double t = o2[sl + e * Lc];
+        q0 = fma(s[e], s[e], q0);
+        q1 = fma(t, s[e], q1);
+        q2 = fma(t, t, q2);
+      }
+      seg_sum3(q0, q1, q2, Lc);
+      bool full = false;
+      if (active) {
+        if (le_nonneg(q0, thr)) {
+          active = false;  // converged on the half step (x has alpha p^)
+        } else if (!is_finite_bits(q1) || !is_finite_bits(q2)) {
+          nonfin = true;
+          active = false;
+        } else if (is_zero_bits(q2)) {
+          broke = true;  // keep the half step, restart
+          active = false;
+        } else {
+          full = true;
+        }
+      }
+      const double om = q1 * recip64(q2);
+      if (full) omega = om;
+#pragma unroll
+      for (int e = 0; e < E; ++e) {
+        const int i = sl + e * Lc;
+        if (full) {
+          xv[e] = fma(om, gs[i], xv[e]);
+          r[e] = fma(-om, o2[i], s[e]);
+          p[e] = fma(-om, o1[i], p[e]);
+        }
+      }
+      double hr = 0.0, rr = 0.0;
+#pragma unroll
+      for (int e = 0; e < E; ++e) {
+        hr = fma(rhs[sl + e * Lc], r[e], hr);
+        rr = fma(r[e], r[e], rr);
+      }
+      seg_sum2(hr, rr, Lc);
+      if (full) {
+        nbreak = 0;
+        if (le_nonneg(rr, thr)) {
+          active = false;
+        } else if (is_zero_bits(om)) {
+          broke = true;
+          active = false;
+        } else {
+          rho_prev = rho;
+          rho = hr;
+        }
+      }
+    }
+    // ---- true residual of the segments that stopped iterating
+#pragma unroll
+    for (int e = 0; e < E; ++e) gs[sl + e * Lc] = xv[e];
+    __syncwarp();
+    seg_spmv(sch, a.L, Lc, As, gs, o1);
+    __syncwarp();
+    double rt2[1] = {0.0};
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+      const int i = sl + e * Lc;
+      const double bi = (has && i < n) ? __ldg(a.b + (size_t)c * n + i) : 0.0;
+      s[e] = bi - o1[i];  // s holds the true residual here
+      rt2[0] = fma(s[e], s[e], rt2[0]);
+    }
+    seg_sum<1>(rt2, Lc);
+    if (fin) {
+      fin = false;
+      resid = sqrt(rt2[0] * recip64(bb));
+      if (nonfin || !is_finite_bits(resid)) {
+        st = CAMP_CELL_NONFINITE;
+      } else if (resid <= tol) {
+        st = CAMP_CELL_CONVERGED;
+      } else if (it >= a.maxit) {
+        st = CAMP_CELL_MAXIT;
+      } else if (broke && ++nbreak >= 2) {
+        st = CAMP_CELL_BREAKDOWN;
+      } else {
+#pragma unroll
+        for (int e = 0; e < E; ++e) r[e] = s[e];
+        restart = true;
+      }
+    }
+    if (!__any_sync(kFull, restart)) break;
+  }
+  // ---- write the cell's results
+  if (has) {
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+      const int i = sl + e * Lc;
+      if (i < n) a.x[(size_t)c * n + i] = xv[e];
+    }
+    if (sl == 0) {
+      a.iters[c] = it;
+      a.resid[c] = resid;
+      if (a.status) a.status[c] = st;
+    }
+  }
+  __syncwarp();
+}
+
+// Plain launch: one mechanism, the SpMV schedule in shared memory, groups of
+// k cells assigned to warps in a grid-stride loop.
 template <int E>
 __global__ void __launch_bounds__(256, CAMP_WARP_MINB)
     warp_bicgstab_kernel(const WarpArgs a) {
@@ -35,278 +308,39 @@ __global__ void __launch_bounds__(256, CAMP_WARP_MINB)
   SchedWord *sch_s = reinterpret_cast<SchedWord *>(smem_raw);
   const int nsch = a.L * a.Lc;
   for (int i = threadIdx.x; i < nsch; i += blockDim.x) sch_s[i] = a.sched[i];
-
+  __syncthreads();
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
-  const int seg = lane >> a.log2Lc;
-  const int sl = lane & (a.Lc - 1);
-  const int segStride = a.segStride;
   double *wbase = reinterpret_cast<double *>(smem_raw + (((size_t)nsch * 8 + 15) & ~(size_t)15)) +
-                  (size_t)warp * a.k * segStride;
-  double *Abase = wbase + (size_t)seg * segStride;
-#if !CAMP_A_GLOBAL
-  double *As = Abase;
-#endif
-  double *gs = Abase + a.segA;   // gathered vector (p^, s^ or x)
-  double *o1 = gs + a.segV;      // v = A p^
-  double *o2 = o1 + a.segV;      // t = A s^
-  double *rhs = o2 + a.segV;     // shadow residual r^
-  double *dvs = rhs + a.segV;    // Jacobi reciprocals
-  for (int i = sl; i < kWarpVectors * a.segV; i += a.Lc) gs[i] = 0.0;
-  __syncthreads();
-  const SchedWord *sch = sch_s + sl;
-
-  const int n = a.n, nnz = a.nnz, Lc = a.Lc;
+                  (size_t)warp * a.k * a.segStride;
+  const SchedWord *sch = sch_s + (lane & (a.Lc - 1));
   const int warps_total = gridDim.x * (blockDim.x >> 5);
-  const double tol = a.tol;
+  for (int g = blockIdx.x * (blockDim.x >> 5) + warp; g < a.ngroups; g += warps_total)
+    solve_group<E, true>(a, g, wbase, sch);
+}
 
-  for (int g = blockIdx.x * (blockDim.x >> 5) + warp; g < a.ngroups;
-       g += warps_total) {
-    const int c = g * a.k + seg;
-    const bool has = c < a.cells;
-    // ---- stage the cell's matrix values (Sec. 3.1: one cell, one team)
-#if CAMP_A_GLOBAL
-    const double *As = a.A + (size_t)(has ? c : 0) * nnz;   // read through L1
-#else
-    if (has) {
-      const double *Ac = a.A + (size_t)c * nnz;
-      if (a.a_perm) {
-        for (int k = sl; k < nnz; k += Lc) As[k] = __ldg(Ac + __ldg(a.a_perm + k));
-      } else {
-        for (int k = sl; k < nnz; k += Lc) As[k] = __ldg(Ac + k);
-      }
-    }
-#endif
-    __syncwarp();
-
-    double r[E], p[E], xv[E], s[E];
-    double bb;
-    {
-      double acc[1] = {0.0};
-#pragma unroll
-      for (int e = 0; e < E; ++e) {
-        const int i = sl + e * Lc;
-        const bool v = has && i < n;
-        const double bi = v ? __ldg(a.b + (size_t)c * n + i) : 0.0;
-        const double d = v ? As[__ldg(a.diag + i)] : 0.0;
-        dvs[i] = v ? (!is_zero_bits(d) ? recip64(d) : 1.0) : 0.0;
-        xv[e] = (v && a.x0_given) ? a.x[(size_t)c * n + i] : 0.0;
-        r[e] = bi;
-        p[e] = 0.0;
-        s[e] = 0.0;
-        acc[0] = fma(bi, bi, acc[0]);
-      }
-      seg_sum<1>(acc, Lc);
-      bb = acc[0];
-    }
-    const double thr = (tol * tol) * bb;  // (tol ||b||)^2
-    int st = -1, it = 0, nbreak = 0;
-    double resid = 0.0;
-    bool done = !has;
-    if (has) {
-      if (!is_finite_bits(bb)) {
-        st = CAMP_CELL_NONFINITE;
-        resid = __longlong_as_double(0x7ff8000000000000ll);
-        done = true;
-      } else if (is_zero_bits(bb)) {
-        st = CAMP_CELL_CONVERGED;
-        done = true;
-#pragma unroll
-        for (int e = 0; e < E; ++e) xv[e] = 0.0;
-      }
-    }
-    if (a.x0_given) {  // r = b - A x0
-#pragma unroll
-      for (int e = 0; e < E; ++e) gs[sl + e * Lc] = xv[e];
-      __syncwarp();
-      seg_spmv(sch, a.L, Lc, As, gs, o1);
-      __syncwarp();
-#pragma unroll
-      for (int e = 0; e < E; ++e) r[e] -= o1[sl + e * Lc];
-    }
-
-    bool restart = !done, first = true;
-    bool fin = false, active = false, broke = false, nonfin = false;
-    double rho = 1.0, rho_prev = 1.0, alpha = 1.0, omega = 1.0;
-    for (;;) {
-      {  // (re)start from the current residual r
-        double acc[1] = {0.0};
-#pragma unroll
-        for (int e = 0; e < E; ++e) acc[0] = fma(r[e], r[e], acc[0]);
-        seg_sum<1>(acc, Lc);
-        if (restart) {
-#pragma unroll
-          for (int e = 0; e < E; ++e) {
-            rhs[sl + e * Lc] = r[e];
-            p[e] = 0.0;
-          }
-          rho = acc[0];
-          rho_prev = alpha = omega = 1.0;
-          broke = nonfin = false;
-          fin = true;
-          // a restart follows a failed true-residual test: always iterate
-          active = first ? !le_nonneg(acc[0], thr) : true;
-          restart = false;
-          first = false;
-        }
-      }
-      while (__any_sync(kFull, active)) {
-        if (active) {
-          if (it >= a.maxit) {
-            active = false;
-          } else if (!is_finite_bits(rho)) {
-            nonfin = true;
-            active = false;
-          } else if (abs_tiny(rho)) {
-            broke = true;
-            active = false;
-          }
-        }
-        // p = r + beta (p - omega v); the bracket is kept in p
-        const double beta = (rho * alpha) * recip64(rho_prev * omega);
-#pragma unroll
-        for (int e = 0; e < E; ++e) {
-          const int i = sl + e * Lc;
-          if (active) p[e] = fma(beta, p[e], r[e]);
-          gs[i] = dvs[i] * p[e];
-        }
-        __syncwarp();
-        seg_spmv(sch, a.L, Lc, As, gs, o1);  // v = A p^
-        __syncwarp();
-        if (active) ++it;
-        double sg[1] = {0.0};
-#pragma unroll
-        for (int e = 0; e < E; ++e) {
-          const int i = sl + e * Lc;
-          sg[0] = fma(rhs[i], o1[i], sg[0]);
-        }
-        seg_sum<1>(sg, Lc);
-        if (active) {
-          if (!is_finite_bits(sg[0])) {
-            nonfin = true;
-            active = false;
-          } else if (abs_tiny(sg[0])) {
-            broke = true;
-            active = false;
-          }
-        }
-        const double al = rho * recip64(sg[0]);
-        if (active) alpha = al;
-#pragma unroll
-        for (int e = 0; e < E; ++e) {
-          const int i = sl + e * Lc;
-          if (active) {
-            xv[e] = fma(al, gs[i], xv[e]);
-            s[e] = fma(-al, o1[i], r[e]);
-          }
-          gs[i] = dvs[i] * s[e];
-        }
-        __syncwarp();
-        seg_spmv(sch, a.L, Lc, As, gs, o2);  // t = A s^
-        __syncwarp();
-        double q0 = 0.0, q1 = 0.0, q2 = 0.0;
-#pragma unroll
-        for (int e = 0; e < E; ++e) {
-          const double t = o2[sl + e * Lc];
-          q0 = fma(s[e], s[e], q0);
-          q1 = fma(t, s[e], q1);
-          q2 = fma(t, t, q2);
-        }
-        seg_sum3(q0, q1, q2, Lc);
-        bool full = false;
-        if (active) {
-          if (le_nonneg(q0, thr)) {
-            active = false;  // converged on the half step (x has alpha p^)
-          } else if (!is_finite_bits(q1) || !is_finite_bits(q2)) {
-            nonfin = true;
-            active = false;
-          } else if (is_zero_bits(q2)) {
-            broke = true;  // keep the half step, restart
-            active = false;
-          } else {
-            full = true;
-          }
-        }
-        const double om = q1 * recip64(q2);
-        if (full) omega = om;
-#pragma unroll
-        for (int e = 0; e < E; ++e) {
-          const int i = sl + e * Lc;
-          if (full) {
-            xv[e] = fma(om, gs[i], xv[e]);
-            r[e] = fma(-om, o2[i], s[e]);
-            p[e] = fma(-om, o1[i], p[e]);
-          }
-        }
-        double hr = 0.0, rr = 0.0;
-#pragma unroll
-        for (int e = 0; e < E; ++e) {
-          hr = fma(rhs[sl + e * Lc], r[e], hr);
-          rr = fma(r[e], r[e], rr);
-        }
-        seg_sum2(hr, rr, Lc);
-        if (full) {
-          nbreak = 0;
-          if (le_nonneg(rr, thr)) {
-            active = false;
-          } else if (is_zero_bits(om)) {
-            broke = true;
-            active = false;
-          } else {
-            rho_prev = rho;
-            rho = hr;
-          }
-        }
-      }
-      // ---- true residual of the segments that stopped iterating
-#pragma unroll
-      for (int e = 0; e < E; ++e) gs[sl + e * Lc] = xv[e];
-      __syncwarp();
-      seg_spmv(sch, a.L, Lc, As, gs, o1);
-      __syncwarp();
-      double rt2[1] = {0.0};
-#pragma unroll
-      for (int e = 0; e < E; ++e) {
-        const int i = sl + e * Lc;
-        const double bi = (has && i < n) ? __ldg(a.b + (size_t)c * n + i) : 0.0;
-        s[e] = bi - o1[i];  // s holds the true residual here
-        rt2[0] = fma(s[e], s[e], rt2[0]);
-      }
-      seg_sum<1>(rt2, Lc);
-      if (fin) {
-        fin = false;
-        resid = sqrt(rt2[0] * recip64(bb));
-        if (nonfin || !is_finite_bits(resid)) {
-          st = CAMP_CELL_NONFINITE;
-        } else if (resid <= tol) {
-          st = CAMP_CELL_CONVERGED;
-        } else if (it >= a.maxit) {
-          st = CAMP_CELL_MAXIT;
-        } else if (broke && ++nbreak >= 2) {
-          st = CAMP_CELL_BREAKDOWN;
-        } else {
-#pragma unroll
-          for (int e = 0; e < E; ++e) r[e] = s[e];
-          restart = true;
-        }
-        if (!restart) done = true;
-      }
-      if (!__any_sync(kFull, restart)) break;
-    }
-    // ---- write the cell's results
-    if (has) {
-#pragma unroll
-      for (int e = 0; e < E; ++e) {
-        const int i = sl + e * Lc;
-        if (i < n) a.x[(size_t)c * n + i] = xv[e];
-      }
-      if (sl == 0) {
-        a.iters[c] = it;
-        a.resid[c] = resid;
-        if (a.status) a.status[c] = st;
-      }
-    }
-    __syncwarp();
+// Persistent launch over several mechanisms (uneven batching): every warp
+// takes the next work item (one group of one mechanism) from a device queue
+// head until the queue is empty.  Items are ordered mechanism by mechanism,
+// largest cells first, so the long items start early and the short ones fill
+// the tail.  The only wait is the atomic increment: no spin, no barrier.
+template <int E, bool ASMEM>
+__global__ void __launch_bounds__(256, CAMP_WARP_MINB)
+    batch_bicgstab_kernel(const __grid_constant__ BatchArgs b) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int lane = threadIdx.x & 31;
+  const int warp = threadIdx.x >> 5;
+  double *wbase = reinterpret_cast<double *>(smem_raw) + (size_t)warp * b.warp_doubles;
+  for (;;) {
+    unsigned item = 0;
+    if (lane == 0) item = atomicAdd(b.counter, 1u);
+    item = __shfl_sync(kFull, item, 0);
+    if (item >= (unsigned)b.total_items) break;
+    int m = 0;
+    while (m + 1 < b.nmech && item >= (unsigned)b.item_begin[m + 1]) ++m;
+    const WarpArgs &a = b.m[m];
+    const SchedWord *sch = a.sched + (lane & (a.Lc - 1));
+    solve_group<E, ASMEM>(a, (int)item - b.item_begin[m], wbase, sch);
   }
 }
 
