@@ -212,6 +212,39 @@ camp_status camp_batch_solve(camp_batch_t b, const int *cells,
                              double *const *resid_out, int *const *status_out);
 
 /*
+ * Solve without allocating device memory (the paper has no counterpart; this
+ * entry point exists for callers that cannot call cudaMalloc -- for example a
+ * host model whose device memory all comes from its own pool, or a time loop
+ * that must not allocate once it runs).  It needs no solver handle: the
+ * pattern (row_ptr [n+1], col_idx [nnz]) is a HOST array as for
+ * camp_solver_create, the other arrays are DEVICE pointers with the layouts
+ * and meaning of camp_solver_solve_ex (status_out may be NULL), and the solve
+ * of every cell is that of camp_solver_solve with the automatic arrangement.
+ * The SpMV schedule and the diagonal positions, which a handle keeps in
+ * device memory of its own, are staged instead into one static device array
+ * of 256 KiB inside the library, which every GPU that loads the library holds
+ * until the process exits; a pattern whose schedule and diagonal positions do
+ * not fit returns CAMP_EUNSUPPORTED before any work is enqueued, as does
+ * n > 512.  No cudaMalloc, cudaFree or other allocating routine is called.
+ *  - The first call on a device performs a one-time set-up with that device
+ *    current (it looks up the device address of the static array); make that
+ *    first call before any stream capture.
+ *  - Every call shares the one static array and overwrites it (it keeps the
+ *    last call's schedule; nothing in it needs to start at zero).  Calls whose
+ *    work overlaps on the GPU -- on different streams, or from different host
+ *    threads -- race on it: order them on one stream.
+ *  - Work is enqueued on `stream` (a cudaStream_t, NULL = legacy default
+ *    stream): two host-to-device copies of the schedule from host memory,
+ *    then the kernel.
+ */
+camp_status camp_solve_noalloc(int n, int nnz, const int *row_ptr,
+                               const int *col_idx, int cells,
+                               const double *A_vals, const double *b,
+                               double *x, double tol, int maxit,
+                               int *iters_out, double *resid_out,
+                               int *status_out, void *stream);
+
+/*
  * Inspect the static SpMV schedule the warp-packed kernels use for a pattern
  * (host only, no GPU needed).  The rows are assigned whole to lanes_per_cell
  * lanes by longest-first bin packing; each lane runs slots_per_lane slots.

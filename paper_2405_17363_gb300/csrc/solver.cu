@@ -860,4 +860,191 @@ camp_status camp_batch_solve(camp_batch_t b, const int *cells,
   return CAMP_OK;
 }
 
+
+// ---- solve without any device allocation -------------------------------
+//
+// For callers that cannot call cudaMalloc: a host model that owns all device
+// memory through its own pool, or a time loop that must not allocate once it
+// runs.  camp_solve_noalloc needs no solver handle: the SpMV schedule and the
+// diagonal positions, which camp_solver_create keeps in device memory of its
+// own, are staged instead in the file-scope array below (kNoAllocScratchBytes,
+// held by every GPU that loads the library until the process exits), and the
+// plain warp kernel reads them from there.
+
+}  // extern "C"
+
+namespace camp {
+namespace {
+constexpr size_t kNoAllocScratchBytes = 256 * 1024;
+constexpr int kNoAllocMaxDevices = 64;
+}  // namespace
+}  // namespace camp
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[camp::kNoAllocScratchBytes];
+
+namespace camp {
+namespace {
+
+std::mutex g_noalloc_mu;                              // guards the host buffers below
+void *g_noalloc_dev[kNoAllocMaxDevices];              // device address of the scratch
+SchedWord g_noalloc_words[kNoAllocScratchBytes / sizeof(SchedWord)];
+int g_noalloc_order[1024], g_noalloc_diag[1024];
+int g_noalloc_bin_rows[32][1024], g_noalloc_bin_count[32];
+long g_noalloc_load[32];
+
+// Same schedule as build_schedule (longest-first bin packing of whole rows,
+// ties to the lower lane, rows ascending within a lane), written into the
+// static host buffer; returns slots per lane or -1 if it does not fit.
+int noalloc_schedule(int n, const int *rp, const int *ci, int Lc, size_t cap_words) {
+  for (int i = 0; i < n; ++i) g_noalloc_order[i] = i;
+  for (int i = 1; i < n; ++i) {  // stable insertion sort, longer rows first
+    const int r = g_noalloc_order[i];
+    const int len = rp[r + 1] - rp[r];
+    int j = i - 1;
+    while (j >= 0 && rp[g_noalloc_order[j] + 1] - rp[g_noalloc_order[j]] < len) {
+      g_noalloc_order[j + 1] = g_noalloc_order[j];
+      --j;
+    }
+    g_noalloc_order[j + 1] = r;
+  }
+  for (int q = 0; q < Lc; ++q) {
+    g_noalloc_load[q] = 0;
+    g_noalloc_bin_count[q] = 0;
+  }
+  for (int i = 0; i < n; ++i) {
+    const int r = g_noalloc_order[i];
+    int best = 0;
+    for (int q = 1; q < Lc; ++q)
+      if (g_noalloc_load[q] < g_noalloc_load[best]) best = q;
+    g_noalloc_load[best] += rp[r + 1] - rp[r];
+    g_noalloc_bin_rows[best][g_noalloc_bin_count[best]++] = r;
+  }
+  long L = 0;
+  for (int q = 0; q < Lc; ++q) L = std::max(L, g_noalloc_load[q]);
+  if ((size_t)L * Lc > cap_words) return -1;
+  for (long w = 0; w < L * Lc; ++w) g_noalloc_words[w] = SchedWord{0u, 0u};
+  for (int q = 0; q < Lc; ++q) {
+    int *rows = g_noalloc_bin_rows[q];
+    const int cnt = g_noalloc_bin_count[q];
+    for (int i = 1; i < cnt; ++i) {  // ascending row order within the lane
+      const int r = rows[i];
+      int j = i - 1;
+      while (j >= 0 && rows[j] > r) {
+        rows[j + 1] = rows[j];
+        --j;
+      }
+      rows[j + 1] = r;
+    }
+    long j = 0;
+    for (int t = 0; t < cnt; ++t) {
+      const int r = rows[t];
+      for (int k = rp[r]; k < rp[r + 1]; ++k, ++j) {
+        SchedWord w;
+        w.x = (unsigned)k | ((unsigned)ci[k] << 16);
+        w.y = (k == rp[r + 1] - 1) ? ((unsigned)r | (1u << 16)) : 0u;
+        g_noalloc_words[j * Lc + q] = w;
+      }
+    }
+  }
+  return (int)L;
+}
+
+}  // namespace
+}  // namespace camp
+
+extern "C" {
+
+camp_status camp_solve_noalloc(int n, int nnz, const int *row_ptr,
+                               const int *col_idx, int cells,
+                               const double *A_vals, const double *b,
+                               double *x, double tol, int maxit,
+                               int *iters_out, double *resid_out,
+                               int *status_out, void *stream) {
+  if (!row_ptr || !col_idx) return fail(CAMP_EINVAL, "null pattern array");
+  if (n < 1 || n > 1024) return fail(CAMP_EINVAL, "n=%d outside [1, 1024]", n);
+  if (nnz < n || nnz > 65535) return fail(CAMP_EINVAL, "nnz=%d outside [n, 65535]", nnz);
+  if (cells < 0) return fail(CAMP_EINVAL, "cells < 0");
+  if (!(tol > 0.0) || !std::isfinite(tol)) return fail(CAMP_EINVAL, "tol must be finite and > 0");
+  if (maxit < 1) return fail(CAMP_EINVAL, "maxit must be >= 1");
+  if (row_ptr[0] != 0 || row_ptr[n] != nnz)
+    return fail(CAMP_EPATTERN, "row_ptr[0] must be 0 and row_ptr[n] must equal nnz");
+  const int Lc = auto_lanes(n, kAutoRowsPerLane);
+  const int E = Lc ? (n + Lc - 1) / Lc : 0;
+  if (Lc == 0 || E > kMaxE)
+    return fail(CAMP_EUNSUPPORTED, "n=%d is too large for the warp kernel (at most %d)", n, 32 * kMaxE);
+  if (cells > 0 && (!A_vals || !b || !x || !iters_out || !resid_out))
+    return fail(CAMP_EINVAL, "null array pointer");
+
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  for (int i = 0; i < n; ++i) {
+    g_noalloc_diag[i] = -1;
+    if (row_ptr[i + 1] < row_ptr[i]) return fail(CAMP_EPATTERN, "row_ptr decreases at row %d", i);
+    for (int k = row_ptr[i]; k < row_ptr[i + 1]; ++k) {
+      const int j = col_idx[k];
+      if (j < 0 || j >= n) return fail(CAMP_EPATTERN, "column %d out of range at entry %d", j, k);
+      if (k > row_ptr[i] && j <= col_idx[k - 1])
+        return fail(CAMP_EPATTERN, "columns not strictly increasing in row %d", i);
+      if (j == i) g_noalloc_diag[i] = k;
+    }
+    if (g_noalloc_diag[i] < 0) return fail(CAMP_EPATTERN, "diagonal entry missing in row %d", i);
+  }
+  const size_t diag_bytes = ((size_t)n * sizeof(int) + 15) & ~(size_t)15;
+  const size_t cap_words = (kNoAllocScratchBytes - diag_bytes) / sizeof(SchedWord);
+  const int L = noalloc_schedule(n, row_ptr, col_idx, Lc, cap_words);
+  if (L < 0)
+    return fail(CAMP_EUNSUPPORTED,
+                "pattern needs more than the %zu-byte static scratch of camp_solve_noalloc "
+                "(schedule %d lanes x slots plus %d diagonal positions); use a solver handle",
+                kNoAllocScratchBytes, Lc, n);
+  if (cells == 0) return CAMP_OK;
+
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+  if (dev < 0 || dev >= kNoAllocMaxDevices) return fail(CAMP_EUNSUPPORTED, "device ordinal %d", dev);
+  if (!g_noalloc_dev[dev]) {  // set-up, once per device, with that device current
+    void *p = nullptr;
+    if ((e = cudaGetSymbolAddress(&p, g_noalloc_scratch)) != cudaSuccess)
+      return cuda_fail(e, "cudaGetSymbolAddress(static scratch)");
+    g_noalloc_dev[dev] = p;
+  }
+  unsigned char *scratch = (unsigned char *)g_noalloc_dev[dev];
+  int sms = 0, optin = 0;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+
+  WarpArgs a;
+  a.cells = cells; a.n = n; a.nnz = nnz;
+  a.Lc = Lc; a.log2Lc = ilog2(Lc); a.k = 32 / Lc; a.L = L;
+  a.segA = (nnz + 1) & ~1;
+  a.segV = ((E * Lc + 1) + 1) & ~1;
+  a.segStride = bank_spread_stride(a.segA + kWarpVectors * a.segV, a.k);
+  a.ngroups = (cells + a.k - 1) / a.k;
+  a.A = A_vals; a.b = b; a.x = x; a.iters = iters_out; a.resid = resid_out;
+  a.status = status_out; a.a_perm = nullptr;
+  a.diag = (const int *)scratch;
+  a.sched = (const SchedWord *)(scratch + diag_bytes);
+  a.tol = tol; a.maxit = maxit; a.x0_given = 0;
+  int wpb = 4;
+  const size_t sch = (((size_t)L * Lc * 8) + 15) & ~(size_t)15;
+  size_t smem = sch + (size_t)wpb * a.k * a.segStride * 8;
+  while (smem > (size_t)optin && wpb > 1) smem = sch + (size_t)(--wpb) * a.k * a.segStride * 8;
+  if (smem > (size_t)optin) return fail(CAMP_EUNSUPPORTED, "cell does not fit in shared memory");
+  int occ = 0;
+  if ((e = warp_occupancy(E, wpb, smem, &occ)) != cudaSuccess) return cuda_fail(e, "occupancy");
+  if (occ < 1) occ = 1;
+  const int grid = std::max(1, std::min((a.ngroups + wpb - 1) / wpb, sms * occ));
+  cudaStream_t st = (cudaStream_t)stream;
+  // stage the diagonal positions and the schedule (pageable source: the call
+  // returns once the host buffers have been consumed)
+  if ((e = cudaMemcpyAsync(scratch, g_noalloc_diag, (size_t)n * sizeof(int),
+                           cudaMemcpyHostToDevice, st)) != cudaSuccess ||
+      (e = cudaMemcpyAsync(scratch + diag_bytes, g_noalloc_words,
+                           (size_t)L * Lc * sizeof(SchedWord), cudaMemcpyHostToDevice, st)) != cudaSuccess)
+    return cuda_fail(e, "staging into the static scratch");
+  if ((e = launch_warp(E, a, wpb, grid, smem, st)) != cudaSuccess)
+    return cuda_fail(e, "warp kernel launch");
+  return CAMP_OK;
+}
+
 }  // extern "C"
