@@ -37,6 +37,10 @@ WORKLOAD_ID = 1
 HBM_PEAK_FALLBACK = 6800.0
 # FP64 pipe: 2 DFMA per clock per SM (4 flops) x 152 SMs x 2.07 GHz max clock
 FP64_PEAK_GFLOPS = 4 * 152 * 2.07
+# DRAM bytes (read + write) per launch of the headline kernel from one ncu
+# capture (dram__bytes_read.sum + dram__bytes_write.sum), valid only for the
+# library revision it was taken on; any other revision reports null.
+TRAFFIC_BYTES = {"campsolve 0.2 (sm_103a)": 51.638e6}
 
 
 def peaks():
@@ -255,6 +259,16 @@ def time_uneven(camp, dev, flush, stream, steps=50):
             "converged": conv, "iters_mean": float(iters.mean()), "iters_max": int(iters.max())}
 
 
+def run_uneven_case(args):
+    """--case uneven: the persistent batch alone, timed as the step."""
+    import torch
+    from paper_2405_17363_gb300 import camp
+    dev = torch.device("cuda", 0)
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+    res = time_uneven(camp, dev, flush, torch.cuda.current_stream(), steps=args.steps)
+    print(json.dumps({"case": "uneven", **res}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -267,6 +281,9 @@ def main():
                     help="auto | warp:<lanes per cell>[:<warps per block>] | block:<cells per block>")
     ap.add_argument("--mode", default="fp64", choices=["fp64", "mixed"],
                     help="fp64: plain FP64 solve (the headline); mixed: FP32-inner refinement")
+    ap.add_argument("--case", default="headline", choices=["headline", "uneven"],
+                    help="headline: the 80-species 10k-cell FP64 solve; uneven: time the "
+                         "persistent multi-mechanism batch as the step (for profiling)")
     ap.add_argument("--skip-extras", action="store_true",
                     help="time the device solve only (no e2e, CPU baseline or mixed side run)")
     args = ap.parse_args()
@@ -279,6 +296,8 @@ def main():
 
     if args.impl == "reference":
         return run_reference(args, rank, world)
+    if args.case == "uneven":
+        return run_uneven_case(args)
 
     import torch
     import torch.distributed as dist
@@ -372,7 +391,8 @@ def main():
             "roofline": {"bound": "alu", "achieved": flops / kernel_s / 1e9,
                          "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s",
                          "frac": flops / kernel_s / 1e9 / FP64_PEAK_GFLOPS,
-                         "traffic": None,
+                         "traffic": TRAFFIC_BYTES.get(camp.camp_version())
+                         if args.arrangement == "auto" and args.mode == "fp64" else None,
                          "peak_source": "FP64 pipe 4 flop/clk/SM x 152 SMs x 2.07 GHz"},
             "hbm_roofline": {"bound": "hbm", "achieved": nbytes / kernel_s / 1e9,
                              "peak": hbm_peak, "unit": "GB/s",
