@@ -22,7 +22,10 @@
  *    handle owns only its device copies of the pattern, the transposed
  *    pattern, the SpMV schedules and its staging buffers.
  *  - Streams.  Work is enqueued on the stream set with camp_solver_set_stream
- *    (default: the legacy default stream) and returns without waiting.
+ *    (default: the legacy default stream) and returns without waiting.  The
+ *    solves of one handle share its device work queue: calls on one handle
+ *    must not overlap on the GPU (keep them on one stream, or use one handle
+ *    per stream); different handles are independent.
  *  - Errors.  A negative camp_status means nothing was enqueued (argument or
  *    pattern error) or the CUDA runtime reported an error; camp_last_error()
  *    gives a message.  Non-convergence of a cell is NOT an error: it shows in

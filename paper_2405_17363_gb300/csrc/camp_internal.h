@@ -35,6 +35,10 @@ struct WarpArgs {
   double tol;
   int maxit;
   int x0_given;
+  // Optional dynamic queue for the plain launch: [0] next group, [1] warps
+  // finished.  The last warp to finish resets both to zero, so the pair is
+  // ready for the next launch in stream order.  Null: static assignment.
+  unsigned int *queue;
 };
 
 // Persistent launch over up to kMaxMech mechanisms: mechanism m owns work

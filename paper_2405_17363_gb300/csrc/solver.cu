@@ -166,6 +166,9 @@ struct camp_solver {
   cudaStream_t stream = nullptr;
   View fwd, tr;
   int *d_row_of = nullptr;  // forward view: row of entry k
+  // dynamic group queues of the warp kernel, one pair per stream the handle
+  // uses: [0..1] its own stream, [2..5] the two streams of solve_host
+  unsigned int *d_queue = nullptr;
   int arrangement = CAMP_ARR_AUTO, lanes = 0, cpb = 1, wpb = 0;
   // staging for camp_solver_solve_host
   double *h_dA = nullptr, *h_db = nullptr, *h_dx = nullptr, *h_dres = nullptr;
@@ -260,7 +263,7 @@ size_t block_smem(int n, int nnz, int cpb, int threads) {
 camp_status do_solve(camp_solver_t h, int cells, const double *A_vals,
                      const double *b, double *x, double tol, int maxit,
                      int *iters_out, double *resid_out, int *status_out,
-                     int flags, cudaStream_t st) {
+                     int flags, cudaStream_t st, int queue_slot) {
   if (!h) return fail(CAMP_EINVAL, "null solver handle");
   if (cells < 0) return fail(CAMP_EINVAL, "cells < 0");
   if (!(tol > 0.0) || !std::isfinite(tol)) return fail(CAMP_EINVAL, "tol must be finite and > 0");
@@ -307,6 +310,7 @@ camp_status do_solve(camp_solver_t h, int cells, const double *A_vals,
     a.status = status_out; a.a_perm = v.d_perm; a.diag = v.d_diag;
     a.sched = S->d_words; a.tol = tol; a.maxit = maxit;
     a.x0_given = (flags & CAMP_X0_GIVEN) ? 1 : 0;
+    a.queue = h->d_queue + 2 * queue_slot;
     int occ = 0;
     e = warp_occupancy(E, wpb, smem, &occ);
     if (e != cudaSuccess) return cuda_fail(e, "occupancy");
@@ -342,7 +346,7 @@ camp_status do_solve(camp_solver_t h, int cells, const double *A_vals,
 extern "C" {
 
 const char *camp_last_error(void) { return g_err.c_str(); }
-const char *camp_version(void) { return "campsolve 0.2 (sm_103a)"; }
+const char *camp_version(void) { return "campsolve 0.3 (sm_103a)"; }
 
 camp_status camp_schedule_build(int n, int nnz, const int *row_ptr,
                                 const int *col_idx, int lanes_per_cell,
@@ -436,10 +440,12 @@ camp_status camp_solver_create(camp_solver_t *out, int n, int nnz,
       (e = upload(&t.d_ci, t.ci)) != cudaSuccess ||
       (e = upload(&t.d_diag, t.diag)) != cudaSuccess ||
       (e = upload(&t.d_perm, t.perm)) != cudaSuccess ||
-      (e = upload(&h->d_row_of, row_of)) != cudaSuccess) {
+      (e = upload(&h->d_row_of, row_of)) != cudaSuccess ||
+      (e = upload(&h->d_queue, std::vector<unsigned int>(6, 0u))) != cudaSuccess) {
     free_view(h->fwd);
     free_view(h->tr);
     cudaFree(h->d_row_of);
+    cudaFree(h->d_queue);
     delete h;
     return cuda_fail(e, "pattern upload");
   }
@@ -454,6 +460,7 @@ camp_status camp_solver_destroy(camp_solver_t h) {
   free_view(h->fwd);
   free_view(h->tr);
   cudaFree(h->d_row_of);
+  cudaFree(h->d_queue);
   cudaFree(h->h_dA); cudaFree(h->h_db); cudaFree(h->h_dx);
   cudaFree(h->h_dres); cudaFree(h->h_dit); cudaFree(h->h_dst);
   for (auto &s : h->h_streams) if (s) cudaStreamDestroy(s);
@@ -504,7 +511,7 @@ camp_status camp_solver_solve(camp_solver_t h, int cells, const double *A_vals,
                               const double *b, double *x, double tol,
                               int maxit, int *iters_out, double *resid_out) {
   return do_solve(h, cells, A_vals, b, x, tol, maxit, iters_out, resid_out,
-                  nullptr, 0, h ? h->stream : nullptr);
+                  nullptr, 0, h ? h->stream : nullptr, 0);
 }
 
 camp_status camp_solver_solve_ex(camp_solver_t h, int cells,
@@ -513,7 +520,7 @@ camp_status camp_solver_solve_ex(camp_solver_t h, int cells,
                                  int *iters_out, double *resid_out,
                                  int *status_out, int flags) {
   return do_solve(h, cells, A_vals, b, x, tol, maxit, iters_out, resid_out,
-                  status_out, flags, h ? h->stream : nullptr);
+                  status_out, flags, h ? h->stream : nullptr, 0);
 }
 
 camp_status camp_solver_grad_A(camp_solver_t h, int cells,
@@ -592,7 +599,7 @@ camp_status camp_solver_solve_host(camp_solver_t h, int cells,
                     (size_t)cn * n * 8, cudaMemcpyHostToDevice, s);
     rs = do_solve(h, cn, h->h_dA + (size_t)c0 * nnz, h->h_db + (size_t)c0 * n,
                   h->h_dx + (size_t)c0 * n, tol, maxit, h->h_dit + c0,
-                  h->h_dres + c0, h->h_dst + c0, 0, s);
+                  h->h_dres + c0, h->h_dst + c0, 0, s, 1 + (q & 1));
     if (rs != CAMP_OK) break;
     cudaMemcpyAsync(x + (size_t)c0 * n, h->h_dx + (size_t)c0 * n,
                     (size_t)cn * n * 8, cudaMemcpyDeviceToHost, s);
@@ -799,7 +806,7 @@ camp_status camp_batch_solve(camp_batch_t b, const int *cells,
     a.A = A_vals[m]; a.b = bvec[m]; a.x = x[m]; a.iters = iters_out[m];
     a.resid = resid_out[m]; a.status = status_out ? status_out[m] : nullptr;
     a.a_perm = nullptr; a.diag = v.d_diag; a.sched = S->d_words;
-    a.tol = tol; a.maxit = maxit; a.x0_given = 0;
+    a.tol = tol; a.maxit = maxit; a.x0_given = 0; a.queue = nullptr;
     args.item_begin[q] = items;
     items += a.ngroups;
     warp_doubles = std::max(warp_doubles, a.k * a.segStride);
@@ -1024,7 +1031,7 @@ camp_status camp_solve_noalloc(int n, int nnz, const int *row_ptr,
   a.status = status_out; a.a_perm = nullptr;
   a.diag = (const int *)scratch;
   a.sched = (const SchedWord *)(scratch + diag_bytes);
-  a.tol = tol; a.maxit = maxit; a.x0_given = 0;
+  a.tol = tol; a.maxit = maxit; a.x0_given = 0; a.queue = nullptr;
   int wpb = 4;
   const size_t sch = (((size_t)L * Lc * 8) + 15) & ~(size_t)15;
   size_t smem = sch + (size_t)wpb * a.k * a.segStride * 8;

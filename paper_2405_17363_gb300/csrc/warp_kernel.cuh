@@ -315,8 +315,28 @@ __global__ void __launch_bounds__(256, CAMP_WARP_MINB)
                   (size_t)warp * a.k * a.segStride;
   const SchedWord *sch = sch_s + (lane & (a.Lc - 1));
   const int warps_total = gridDim.x * (blockDim.x >> 5);
-  for (int g = blockIdx.x * (blockDim.x >> 5) + warp; g < a.ngroups; g += warps_total)
-    solve_group<E, true>(a, g, wbase, sch);
+  if (!a.queue) {
+    for (int g = blockIdx.x * (blockDim.x >> 5) + warp; g < a.ngroups; g += warps_total)
+      solve_group<E, true>(a, g, wbase, sch);
+    return;
+  }
+  // dynamic assignment: warps take the next group until none is left
+  for (;;) {
+    unsigned g = 0;
+    if (lane == 0) g = atomicAdd(a.queue, 1u);
+    g = __shfl_sync(kFull, g, 0);
+    if (g >= (unsigned)a.ngroups) break;
+    solve_group<E, true>(a, (int)g, wbase, sch);
+  }
+  if (lane == 0) {
+    // every other warp has taken its last group before counting itself done,
+    // so the last one may reset the queue for the next launch
+    __threadfence();
+    if (atomicAdd(a.queue + 1, 1u) == (unsigned)warps_total - 1u) {
+      atomicExch(a.queue, 0u);
+      atomicExch(a.queue + 1, 0u);
+    }
+  }
 }
 
 // Persistent launch over several mechanisms (uneven batching): every warp
