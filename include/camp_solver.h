@@ -253,11 +253,12 @@ camp_status camp_solve_noalloc(int n, int nnz, const int *row_ptr,
  * lanes by longest-first bin packing; each lane runs slots_per_lane slots.
  * words (host, may be NULL to query slots_per_lane only) receives
  * slots_per_lane * lanes_per_cell slots laid out [slot][lane], two uint32 per
- * slot: word0 = entry index k | column << 16, word1 = row | 1 << 16 on the
- * last entry of a row (store the running sum to that row), else 0; padding
- * slots are (0, 0) and their sums are discarded.  capacity_slots is the
- * number of slots words can hold.  Pattern requirements as for
- * camp_solver_create (validation is lighter: sizes only).
+ * slot: word0 = the entry k (pattern order) whose value the slot multiplies,
+ * or 0xFFFFFFFF for a padding slot; word1 = column (bits 0-10) | row
+ * (bits 11-21) | 1 << 31 on the last entry of a row (store the running sum to
+ * that row).  Padding slots contribute zero.  The kernels stage each cell's
+ * matrix values in this slot order.  capacity_slots is the number of slots
+ * words can hold.  Pattern requirements as for camp_solver_create.
  */
 camp_status camp_schedule_build(int n, int nnz, const int *row_ptr,
                                 const int *col_idx, int lanes_per_cell,

@@ -7,12 +7,21 @@
 
 namespace camp {
 
-// SpMV schedule slot (see build_schedule in solver.cu):
-//   x = a_idx | col << 16            (A value index in the cell, gathered column)
-//   y = row | end << 16              (row stored when end == 1)
-// Words are laid out [slot j][lane-in-cell sl] so a cell's lanes read
-// consecutive words.
-typedef uint2 SchedWord;
+// SpMV schedule slot (see build_schedule in solver.cu), laid out
+// [slot j][lane-in-cell sl] so a cell's lanes read consecutive words:
+//   col (bits 0-10) | row (bits 11-21) | end (bit 31): the slot multiplies the
+//   gathered vector's entry col; on the last slot of a row (end) the running
+//   sum is stored to row.  Alongside, src[j][sl] is the entry of the cell's
+//   A row (pattern order) that slot uses, or -1 for padding: each cell's A is
+//   staged in slot order, so lanes read consecutive shared-memory words.
+typedef unsigned int SchedWord;
+constexpr unsigned kSlotEnd = 0x80000000u;
+// Bytes the plain launches reserve at the start of dynamic shared memory for
+// nsch schedule words (rounded to 16); the host sizes the allocation and the
+// kernels place their per-warp regions with this one function.
+__host__ __device__ inline size_t sched_smem_bytes(int nsch) {
+  return (((size_t)nsch * sizeof(SchedWord)) + 15) & ~(size_t)15;
+}
 
 // Arguments of the warp-packed kernel: Lc lanes per cell, k = 32/Lc cells per
 // warp ("segments"), E rows per lane (template), one group of k consecutive
@@ -29,9 +38,11 @@ struct WarpArgs {
   int *iters;              // [cells]
   double *resid;           // [cells]
   int *status;             // [cells] or null
-  const int *a_perm;       // null, or [nnz]: cell value k of this view = A[c][a_perm[k]]
-  const int *diag;         // [n] position of the diagonal in this view
-  const SchedWord *sched;  // [L x Lc]
+  const SchedWord *sched;  // [L x Lc] slot words
+  const int *src;          // [L x Lc] A entry of each slot (transposed view: permuted), -1 pad
+  const int *dst;          // [nnz] slot of each A entry (pattern order): inverse of src
+  const int *padfrom;      // [Lc] first padding slot of each lane
+  const int *dslot;        // [n] slot of each row's diagonal entry
   double tol;
   int maxit;
   int x0_given;
@@ -115,8 +126,11 @@ struct MixedArgs {
   int *sweeps;    // outer sweeps (or null)
   double *resid;  // final FP64 true relative residual
   int *status;    // or null
-  const int *diag;
   const SchedWord *sched;
+  const int *src;
+  const int *dst;
+  const int *padfrom;
+  const int *dslot;
   double tol;
   int max_sweeps;
   float tol_in;

@@ -27,7 +27,7 @@ __global__ void __launch_bounds__(256, 2) mixed_refine_kernel(const MixedArgs a)
   const int Lc = a.Lc, n = a.n, nnz = a.nnz;
   // bytes per cell: 12 segA + 16 segV + 12 segV (FP64 A, FP32 A, 2 FP64 + 3 FP32 vectors)
   const size_t cellBytes = (size_t)12 * a.segA + (size_t)28 * a.segV;
-  unsigned char *wb = smem_raw + (((size_t)nsch * 8 + 15) & ~(size_t)15) +
+  unsigned char *wb = smem_raw + sched_smem_bytes(nsch) +
                       ((size_t)warp * a.k + seg) * cellBytes;
   double *As = reinterpret_cast<double *>(wb);
   double *g64 = As + a.segA;
@@ -46,12 +46,18 @@ __global__ void __launch_bounds__(256, 2) mixed_refine_kernel(const MixedArgs a)
   for (int g = blockIdx.x * (blockDim.x >> 5) + warp; g < a.ngroups; g += warps_total) {
     const int c = g * a.k + seg;
     const bool has = c < a.cells;
-    if (has) {
-      const double *Ac = a.A + (size_t)c * nnz;
+    {  // stage A in slot order, FP64 and its FP32 rounding
+      const double *Ac = a.A + (size_t)(has ? c : 0) * nnz;
+      const int LL = a.L * Lc;
       for (int k = sl; k < nnz; k += Lc) {
-        const double v = __ldg(Ac + k);
-        As[k] = v;
-        As32[k] = d2f_rn(v);
+        const double v = has ? __ldg(Ac + k) : 0.0;
+        const int t = __ldg(a.dst + k);
+        As[t] = v;
+        As32[t] = d2f_rn(v);
+      }
+      for (int t = __ldg(a.padfrom + sl) * Lc + sl; t < LL; t += Lc) {
+        As[t] = 0.0;
+        As32[t] = 0.0f;
       }
     }
     __syncwarp();
@@ -65,7 +71,7 @@ __global__ void __launch_bounds__(256, 2) mixed_refine_kernel(const MixedArgs a)
         const int i = sl + e * Lc;
         const bool v = has && i < n;
         const double bi = v ? __ldg(a.b + (size_t)c * n + i) : 0.0;
-        const float d = v ? As32[__ldg(a.diag + i)] : 0.0f;
+        const float d = v ? As32[__ldg(a.dslot + i)] : 0.0f;
         dinv[e] = v ? (d != 0.0f ? 1.0f / d : 1.0f) : 0.0f;
         xv[e] = 0.0;
         acc[0] = fma(bi, bi, acc[0]);
@@ -92,7 +98,7 @@ __global__ void __launch_bounds__(256, 2) mixed_refine_kernel(const MixedArgs a)
 #pragma unroll
         for (int e = 0; e < E; ++e) g64[sl + e * Lc] = xv[e];
         __syncwarp();
-        seg_spmv(sch, a.L, Lc, As, g64, o64);
+        seg_spmv(sch, a.L, Lc, As + sl, g64, o64);
         __syncwarp();
       }
       double rr[1] = {0.0};
@@ -162,7 +168,7 @@ __global__ void __launch_bounds__(256, 2) mixed_refine_kernel(const MixedArgs a)
           g32[sl + e * Lc] = dinv[e] * p[e];
         }
         __syncwarp();
-        seg_spmvf(sch, a.L, Lc, As32, g32, o1);
+        seg_spmvf(sch, a.L, Lc, As32 + sl, g32, o1);
         __syncwarp();
         if (act) ++it;
         float sg[1] = {0.0f};
@@ -182,7 +188,7 @@ __global__ void __launch_bounds__(256, 2) mixed_refine_kernel(const MixedArgs a)
           g32[i] = dinv[e] * s[e];
         }
         __syncwarp();
-        seg_spmvf(sch, a.L, Lc, As32, g32, o2);
+        seg_spmvf(sch, a.L, Lc, As32 + sl, g32, o2);
         __syncwarp();
         float q3[3] = {0.0f, 0.0f, 0.0f};
 #pragma unroll

@@ -12,9 +12,6 @@
 #include <vector>
 
 #include "camp_internal.h"
-#ifndef CAMP_A_GLOBAL
-#define CAMP_A_GLOBAL 0
-#endif
 
 namespace camp {
 cudaError_t launch_warp_1(const WarpArgs &, int, int, size_t, cudaStream_t);
@@ -95,15 +92,24 @@ camp_status cuda_fail(cudaError_t e, const char *where) {
 
 // Balanced static SpMV schedule for lanes_per_cell lanes: whole rows are
 // assigned to lanes by longest-processing-time-first bin packing, then each
-// lane's rows are listed entry by entry and padded to the longest lane.
+// lane's rows are listed entry by entry and padded to the longest lane.  For
+// every slot: the packed word (column, row, end of row), the entry of the
+// cell's A row it multiplies (src; the transposed view maps through its
+// permutation), and for every row the slot of its diagonal entry.
 struct Schedule {
   int Lc = 0, L = 0;
   std::vector<SchedWord> words;  // [L][Lc]
+  std::vector<int> src;          // [L][Lc], -1 = padding
+  std::vector<int> dslot;        // [n]
+  std::vector<int> dst;          // [nnz] slot of each A entry (forward order)
+  std::vector<int> padfrom;      // [Lc] first padding slot of each lane
   SchedWord *d_words = nullptr;
+  int *d_src = nullptr, *d_dslot = nullptr, *d_dst = nullptr, *d_padfrom = nullptr;
 };
 
 Schedule build_schedule(int n, const std::vector<int> &rp,
-                        const std::vector<int> &ci, int Lc) {
+                        const std::vector<int> &ci, const std::vector<int> &perm,
+                        const std::vector<int> &diag, int Lc) {
   std::vector<int> order(n);
   std::iota(order.begin(), order.end(), 0);
   std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
@@ -121,16 +127,23 @@ Schedule build_schedule(int n, const std::vector<int> &rp,
   Schedule S;
   S.Lc = Lc;
   S.L = (int)*std::max_element(load.begin(), load.end());
-  S.words.assign((size_t)S.L * Lc, SchedWord{0u, 0u});
+  S.words.assign((size_t)S.L * Lc, 0u);
+  S.src.assign((size_t)S.L * Lc, -1);
+  S.dslot.assign(n, -1);
+  S.dst.assign(rp[n], -1);
+  S.padfrom.assign(Lc, 0);
   for (int q = 0; q < Lc; ++q) {
+    S.padfrom[q] = (int)load[q];
     std::sort(rows[q].begin(), rows[q].end());
     int j = 0;
     for (int r : rows[q])
       for (int k = rp[r]; k < rp[r + 1]; ++k, ++j) {
-        SchedWord w;
-        w.x = (unsigned)k | ((unsigned)ci[k] << 16);
-        w.y = (k == rp[r + 1] - 1) ? ((unsigned)r | (1u << 16)) : 0u;
-        S.words[(size_t)j * Lc + q] = w;
+        const size_t t = (size_t)j * Lc + q;
+        S.words[t] = (unsigned)ci[k] | ((unsigned)r << 11) |
+                     (k == rp[r + 1] - 1 ? kSlotEnd : 0u);
+        S.src[t] = perm.empty() ? k : perm[k];
+        S.dst[S.src[t]] = (int)t;
+        if (k == diag[r]) S.dslot[r] = (int)t;
       }
   }
   return S;
@@ -184,9 +197,20 @@ namespace {
 cudaError_t view_schedule(View &v, int Lc, Schedule **out) {
   auto it = v.sched.find(Lc);
   if (it == v.sched.end()) {
-    Schedule S = build_schedule(v.n, v.rp, v.ci, Lc);
+    Schedule S = build_schedule(v.n, v.rp, v.ci, v.perm, v.diag, Lc);
     cudaError_t e = upload(&S.d_words, S.words);
-    if (e != cudaSuccess) return e;
+    if (e == cudaSuccess) e = upload(&S.d_src, S.src);
+    if (e == cudaSuccess) e = upload(&S.d_dslot, S.dslot);
+    if (e == cudaSuccess) e = upload(&S.d_dst, S.dst);
+    if (e == cudaSuccess) e = upload(&S.d_padfrom, S.padfrom);
+    if (e != cudaSuccess) {
+      cudaFree(S.d_words);
+      cudaFree(S.d_src);
+      cudaFree(S.d_dslot);
+      cudaFree(S.d_dst);
+      cudaFree(S.d_padfrom);
+      return e;
+    }
     it = v.sched.emplace(Lc, std::move(S)).first;
   }
   *out = &it->second;
@@ -198,7 +222,13 @@ void free_view(View &v) {
   cudaFree(v.d_ci);
   cudaFree(v.d_diag);
   cudaFree(v.d_perm);
-  for (auto &kv : v.sched) cudaFree(kv.second.d_words);
+  for (auto &kv : v.sched) {
+    cudaFree(kv.second.d_words);
+    cudaFree(kv.second.d_src);
+    cudaFree(kv.second.d_dslot);
+    cudaFree(kv.second.d_dst);
+    cudaFree(kv.second.d_padfrom);
+  }
   v.sched.clear();
 }
 
@@ -224,23 +254,19 @@ size_t warp_smem(const View &v, int Lc, int L, int wpb, int *segA, int *segV,
                  int *segStride) {
   const int k = 32 / Lc;
   const int E = (v.n + Lc - 1) / Lc;
-#if CAMP_A_GLOBAL
-  *segA = 0;
-#else
-  *segA = (v.nnz + 1) & ~1;
-#endif
+  *segA = (L * Lc + 1) & ~1;  // A in slot order
   *segV = ((E * Lc + 1) + 1) & ~1;
   *segStride = bank_spread_stride(*segA + kWarpVectors * *segV, k);
-  const size_t sch = (((size_t)L * Lc * 8) + 15) & ~(size_t)15;
+  const size_t sch = sched_smem_bytes(L * Lc);
   return sch + (size_t)wpb * k * (size_t)*segStride * 8;
 }
 
 size_t mixed_smem(const View &v, int Lc, int L, int wpb, int *segA, int *segV) {
   const int k = 32 / Lc;
   const int E = (v.n + Lc - 1) / Lc;
-  *segA = (v.nnz + 1) & ~1;
+  *segA = (L * Lc + 1) & ~1;  // A in slot order
   *segV = ((E * Lc + 1) + 1) & ~1;
-  const size_t sch = (((size_t)L * Lc * 8) + 15) & ~(size_t)15;
+  const size_t sch = sched_smem_bytes(L * Lc);
   return sch + (size_t)wpb * k * ((size_t)12 * *segA + (size_t)28 * *segV);
 }
 
@@ -307,8 +333,9 @@ camp_status do_solve(camp_solver_t h, int cells, const double *A_vals,
     a.segA = segA; a.segV = segV; a.segStride = segStride;
     a.ngroups = (cells + a.k - 1) / a.k;
     a.A = A_vals; a.b = b; a.x = x; a.iters = iters_out; a.resid = resid_out;
-    a.status = status_out; a.a_perm = v.d_perm; a.diag = v.d_diag;
-    a.sched = S->d_words; a.tol = tol; a.maxit = maxit;
+    a.status = status_out; a.sched = S->d_words; a.src = S->d_src;
+    a.dst = S->d_dst; a.padfrom = S->d_padfrom;
+    a.dslot = S->d_dslot; a.tol = tol; a.maxit = maxit;
     a.x0_given = (flags & CAMP_X0_GIVEN) ? 1 : 0;
     a.queue = h->d_queue + 2 * queue_slot;
     int occ = 0;
@@ -346,7 +373,7 @@ camp_status do_solve(camp_solver_t h, int cells, const double *A_vals,
 extern "C" {
 
 const char *camp_last_error(void) { return g_err.c_str(); }
-const char *camp_version(void) { return "campsolve 0.3 (sm_103a)"; }
+const char *camp_version(void) { return "campsolve 0.4 (sm_103a)"; }
 
 camp_status camp_schedule_build(int n, int nnz, const int *row_ptr,
                                 const int *col_idx, int lanes_per_cell,
@@ -354,21 +381,26 @@ camp_status camp_schedule_build(int n, int nnz, const int *row_ptr,
                                 int *slots_per_lane) {
   if (!row_ptr || !col_idx || !slots_per_lane)
     return fail(CAMP_EINVAL, "null argument");
-  if (n < 1 || nnz < n || nnz > 65535 || row_ptr[n] != nnz)
+  if (n < 1 || n > 1024 || nnz < n || nnz > 65535 || row_ptr[n] != nnz)
     return fail(CAMP_EINVAL, "bad sizes");
   if (lanes_per_cell < 1 || lanes_per_cell > 32 ||
       (lanes_per_cell & (lanes_per_cell - 1)))
     return fail(CAMP_EINVAL, "lanes_per_cell must be a power of two in [1, 32]");
-  std::vector<int> rp(row_ptr, row_ptr + n + 1), ci(col_idx, col_idx + nnz);
-  Schedule S = build_schedule(n, rp, ci, lanes_per_cell);
+  std::vector<int> rp(row_ptr, row_ptr + n + 1), ci(col_idx, col_idx + nnz), diag(n, -1);
+  for (int i = 0; i < n; ++i) {
+    for (int k = rp[i]; k < rp[i + 1]; ++k)
+      if (ci[k] == i) diag[i] = k;
+    if (diag[i] < 0) return fail(CAMP_EPATTERN, "diagonal entry missing in row %d", i);
+  }
+  Schedule S = build_schedule(n, rp, ci, std::vector<int>(), diag, lanes_per_cell);
   *slots_per_lane = S.L;
   if (words) {
     if ((long)S.L * lanes_per_cell > (long)capacity_slots)
       return fail(CAMP_EINVAL, "capacity %d < %d slots", capacity_slots,
                   S.L * lanes_per_cell);
     for (size_t q = 0; q < S.words.size(); ++q) {
-      words[2 * q] = S.words[q].x;
-      words[2 * q + 1] = S.words[q].y;
+      words[2 * q] = (unsigned)S.src[q];
+      words[2 * q + 1] = S.words[q];
     }
   }
   return CAMP_OK;
@@ -652,7 +684,8 @@ camp_status camp_solver_solve_mixed(camp_solver_t h, int cells,
   a.Lc = Lc; a.log2Lc = ilog2(Lc); a.k = 32 / Lc; a.L = S->L;
   a.segA = segA; a.segV = segV; a.ngroups = (cells + a.k - 1) / a.k;
   a.A = A_vals; a.b = b; a.x = x; a.iters = iters_out; a.sweeps = sweeps_out;
-  a.resid = resid_out; a.status = status_out; a.diag = v.d_diag; a.sched = S->d_words;
+  a.resid = resid_out; a.status = status_out; a.sched = S->d_words; a.src = S->d_src;
+  a.dst = S->d_dst; a.padfrom = S->d_padfrom; a.dslot = S->d_dslot;
   a.tol = tol; a.max_sweeps = max_sweeps; a.tol_in = (float)tol_inner;
   a.maxit_in = maxit_inner;
   int occ = 0;
@@ -799,13 +832,14 @@ camp_status camp_batch_solve(camp_batch_t b, const int *cells,
     WarpArgs &a = args.m[q];
     a.cells = cells[m]; a.n = v.n; a.nnz = v.nnz;
     a.Lc = Lc; a.log2Lc = ilog2(Lc); a.k = 32 / Lc; a.L = S->L;
-    a.segA = asmem ? ((v.nnz + 1) & ~1) : 0;
+    a.segA = asmem ? ((S->L * Lc + 1) & ~1) : 0;
     a.segV = ((E * Lc + 1) + 1) & ~1;
     a.segStride = bank_spread_stride(a.segA + kWarpVectors * a.segV, a.k);
     a.ngroups = (cells[m] + a.k - 1) / a.k;
     a.A = A_vals[m]; a.b = bvec[m]; a.x = x[m]; a.iters = iters_out[m];
     a.resid = resid_out[m]; a.status = status_out ? status_out[m] : nullptr;
-    a.a_perm = nullptr; a.diag = v.d_diag; a.sched = S->d_words;
+    a.sched = S->d_words; a.src = S->d_src; a.dslot = S->d_dslot;
+    a.dst = S->d_dst; a.padfrom = S->d_padfrom;
     a.tol = tol; a.maxit = maxit; a.x0_given = 0; a.queue = nullptr;
     args.item_begin[q] = items;
     items += a.ngroups;
@@ -895,14 +929,18 @@ namespace {
 std::mutex g_noalloc_mu;                              // guards the host buffers below
 void *g_noalloc_dev[kNoAllocMaxDevices];              // device address of the scratch
 SchedWord g_noalloc_words[kNoAllocScratchBytes / sizeof(SchedWord)];
-int g_noalloc_order[1024], g_noalloc_diag[1024];
+int g_noalloc_dst[kNoAllocScratchBytes / sizeof(int)];
+int g_noalloc_padfrom[32];
+int g_noalloc_order[1024], g_noalloc_diag[1024], g_noalloc_dslot[1024];
 int g_noalloc_bin_rows[32][1024], g_noalloc_bin_count[32];
 long g_noalloc_load[32];
 
 // Same schedule as build_schedule (longest-first bin packing of whole rows,
 // ties to the lower lane, rows ascending within a lane), written into the
-// static host buffer; returns slots per lane or -1 if it does not fit.
-int noalloc_schedule(int n, const int *rp, const int *ci, int Lc, size_t cap_words) {
+// static host buffers (slot words, slot of every entry, first padding slot of
+// every lane, slot of every diagonal); returns slots per lane or -1 if it needs
+// more than cap_slots slots.
+int noalloc_schedule(int n, const int *rp, const int *ci, int Lc, size_t cap_slots) {
   for (int i = 0; i < n; ++i) g_noalloc_order[i] = i;
   for (int i = 1; i < n; ++i) {  // stable insertion sort, longer rows first
     const int r = g_noalloc_order[i];
@@ -928,9 +966,10 @@ int noalloc_schedule(int n, const int *rp, const int *ci, int Lc, size_t cap_wor
   }
   long L = 0;
   for (int q = 0; q < Lc; ++q) L = std::max(L, g_noalloc_load[q]);
-  if ((size_t)L * Lc > cap_words) return -1;
-  for (long w = 0; w < L * Lc; ++w) g_noalloc_words[w] = SchedWord{0u, 0u};
+  if ((size_t)L * Lc > cap_slots) return -1;
+  for (long w = 0; w < L * Lc; ++w) g_noalloc_words[w] = 0u;
   for (int q = 0; q < Lc; ++q) {
+    g_noalloc_padfrom[q] = (int)g_noalloc_load[q];
     int *rows = g_noalloc_bin_rows[q];
     const int cnt = g_noalloc_bin_count[q];
     for (int i = 1; i < cnt; ++i) {  // ascending row order within the lane
@@ -946,10 +985,11 @@ int noalloc_schedule(int n, const int *rp, const int *ci, int Lc, size_t cap_wor
     for (int t = 0; t < cnt; ++t) {
       const int r = rows[t];
       for (int k = rp[r]; k < rp[r + 1]; ++k, ++j) {
-        SchedWord w;
-        w.x = (unsigned)k | ((unsigned)ci[k] << 16);
-        w.y = (k == rp[r + 1] - 1) ? ((unsigned)r | (1u << 16)) : 0u;
-        g_noalloc_words[j * Lc + q] = w;
+        const long slot = j * Lc + q;
+        g_noalloc_words[slot] = (unsigned)ci[k] | ((unsigned)r << 11) |
+                                (k == rp[r + 1] - 1 ? kSlotEnd : 0u);
+        g_noalloc_dst[k] = (int)slot;
+        if (k == g_noalloc_diag[r]) g_noalloc_dslot[r] = (int)slot;
       }
     }
   }
@@ -995,9 +1035,17 @@ camp_status camp_solve_noalloc(int n, int nnz, const int *row_ptr,
     }
     if (g_noalloc_diag[i] < 0) return fail(CAMP_EPATTERN, "diagonal entry missing in row %d", i);
   }
+  // scratch layout, 16-byte aligned pieces: [diagonal slots, n ints]
+  // [first padding slot per lane, 32 ints][slot of every entry, nnz ints]
+  // [slot words, L*Lc]
   const size_t diag_bytes = ((size_t)n * sizeof(int) + 15) & ~(size_t)15;
-  const size_t cap_words = (kNoAllocScratchBytes - diag_bytes) / sizeof(SchedWord);
-  const int L = noalloc_schedule(n, row_ptr, col_idx, Lc, cap_words);
+  const size_t pad_bytes = 32 * sizeof(int);
+  const size_t dst_bytes = ((size_t)nnz * sizeof(int) + 15) & ~(size_t)15;
+  const size_t head_bytes = diag_bytes + pad_bytes + dst_bytes;
+  const size_t cap_slots = head_bytes < kNoAllocScratchBytes
+                               ? (kNoAllocScratchBytes - head_bytes) / sizeof(SchedWord)
+                               : 0;
+  const int L = noalloc_schedule(n, row_ptr, col_idx, Lc, cap_slots);
   if (L < 0)
     return fail(CAMP_EUNSUPPORTED,
                 "pattern needs more than the %zu-byte static scratch of camp_solve_noalloc "
@@ -1023,17 +1071,20 @@ camp_status camp_solve_noalloc(int n, int nnz, const int *row_ptr,
   WarpArgs a;
   a.cells = cells; a.n = n; a.nnz = nnz;
   a.Lc = Lc; a.log2Lc = ilog2(Lc); a.k = 32 / Lc; a.L = L;
-  a.segA = (nnz + 1) & ~1;
+  a.segA = (L * Lc + 1) & ~1;
   a.segV = ((E * Lc + 1) + 1) & ~1;
   a.segStride = bank_spread_stride(a.segA + kWarpVectors * a.segV, a.k);
   a.ngroups = (cells + a.k - 1) / a.k;
   a.A = A_vals; a.b = b; a.x = x; a.iters = iters_out; a.resid = resid_out;
-  a.status = status_out; a.a_perm = nullptr;
-  a.diag = (const int *)scratch;
-  a.sched = (const SchedWord *)(scratch + diag_bytes);
+  a.status = status_out;
+  a.dslot = (const int *)scratch;
+  a.padfrom = (const int *)(scratch + diag_bytes);
+  a.dst = (const int *)(scratch + diag_bytes + pad_bytes);
+  a.sched = (const SchedWord *)(scratch + head_bytes);
+  a.src = nullptr;  // only the global-memory A path reads it
   a.tol = tol; a.maxit = maxit; a.x0_given = 0; a.queue = nullptr;
   int wpb = 4;
-  const size_t sch = (((size_t)L * Lc * 8) + 15) & ~(size_t)15;
+  const size_t sch = sched_smem_bytes(L * Lc);
   size_t smem = sch + (size_t)wpb * a.k * a.segStride * 8;
   while (smem > (size_t)optin && wpb > 1) smem = sch + (size_t)(--wpb) * a.k * a.segStride * 8;
   if (smem > (size_t)optin) return fail(CAMP_EUNSUPPORTED, "cell does not fit in shared memory");
@@ -1042,11 +1093,15 @@ camp_status camp_solve_noalloc(int n, int nnz, const int *row_ptr,
   if (occ < 1) occ = 1;
   const int grid = std::max(1, std::min((a.ngroups + wpb - 1) / wpb, sms * occ));
   cudaStream_t st = (cudaStream_t)stream;
-  // stage the diagonal positions and the schedule (pageable source: the call
-  // returns once the host buffers have been consumed)
-  if ((e = cudaMemcpyAsync(scratch, g_noalloc_diag, (size_t)n * sizeof(int),
+  // stage the schedule pieces (pageable source: each call returns once its
+  // host buffer has been consumed)
+  if ((e = cudaMemcpyAsync(scratch, g_noalloc_dslot, (size_t)n * sizeof(int),
                            cudaMemcpyHostToDevice, st)) != cudaSuccess ||
-      (e = cudaMemcpyAsync(scratch + diag_bytes, g_noalloc_words,
+      (e = cudaMemcpyAsync(scratch + diag_bytes, g_noalloc_padfrom, (size_t)Lc * sizeof(int),
+                           cudaMemcpyHostToDevice, st)) != cudaSuccess ||
+      (e = cudaMemcpyAsync(scratch + diag_bytes + pad_bytes, g_noalloc_dst,
+                           (size_t)nnz * sizeof(int), cudaMemcpyHostToDevice, st)) != cudaSuccess ||
+      (e = cudaMemcpyAsync(scratch + head_bytes, g_noalloc_words,
                            (size_t)L * Lc * sizeof(SchedWord), cudaMemcpyHostToDevice, st)) != cudaSuccess)
     return cuda_fail(e, "staging into the static scratch");
   if ((e = launch_warp(E, a, wpb, grid, smem, st)) != cudaSuccess)

@@ -87,7 +87,8 @@ __device__ __forceinline__ void seg_sum3(double &a, double &b, double &c, int Lc
   a = va; b = vb; c = vc;
 }
 
-// o[row] = sum_k A_s[k] g[col k] over this lane's slots of the schedule.
+// o[row] = sum over this lane's slots of A_slot * g[col].  sch and As point at
+// this lane's column of the schedule and of the slot-ordered A (stride Lc).
 __device__ __forceinline__ void seg_spmv(const SchedWord *__restrict__ sch,
                                          int L, int Lc,
                                          const double *__restrict__ As,
@@ -97,9 +98,29 @@ __device__ __forceinline__ void seg_spmv(const SchedWord *__restrict__ sch,
 #pragma unroll kSpmvUnroll
   for (int j = 0; j < L; ++j) {
     const SchedWord w = sch[j * Lc];
-    acc = fma(As[w.x & 0xffffu], gs[w.x >> 16], acc);
-    if (w.y >> 16) {
-      os[w.y & 0xffffu] = acc;
+    acc = fma(As[j * Lc], gs[w & 0x7ffu], acc);
+    if (w & kSlotEnd) {
+      os[(w >> 11) & 0x7ffu] = acc;
+      acc = 0.0;
+    }
+  }
+}
+
+// Same with A read from global memory through the slot's source entry.
+__device__ __forceinline__ void seg_spmv_gather(const SchedWord *__restrict__ sch,
+                                                const int *__restrict__ src,
+                                                int L, int Lc,
+                                                const double *__restrict__ Ag,
+                                                const double *__restrict__ gs,
+                                                double *__restrict__ os) {
+  double acc = 0.0;
+#pragma unroll kSpmvUnroll
+  for (int j = 0; j < L; ++j) {
+    const SchedWord w = sch[j * Lc];
+    const int k = __ldg(src + j * Lc);
+    acc = fma(k >= 0 ? __ldg(Ag + k) : 0.0, gs[w & 0x7ffu], acc);
+    if (w & kSlotEnd) {
+      os[(w >> 11) & 0x7ffu] = acc;
       acc = 0.0;
     }
   }
@@ -114,17 +135,19 @@ __device__ __forceinline__ void seg_sumf(float (&v)[NV], int Lc) {
   }
 }
 
-// o[row] = sum_k A_s[k] g[col k] in FP32 (same schedule).
+// FP32 variant (slot-ordered A32).
 __device__ __forceinline__ void seg_spmvf(const SchedWord *__restrict__ sch,
-                                          int L, int Lc, const float *As,
-                                          const float *gs, float *os) {
+                                          int L, int Lc,
+                                          const float *__restrict__ As,
+                                          const float *__restrict__ gs,
+                                          float *__restrict__ os) {
   float acc = 0.0f;
-#pragma unroll 4
+#pragma unroll kSpmvUnroll
   for (int j = 0; j < L; ++j) {
     const SchedWord w = sch[j * Lc];
-    acc = fmaf(As[w.x & 0xffffu], gs[w.x >> 16], acc);
-    if (w.y >> 16) {
-      os[w.y & 0xffffu] = acc;
+    acc = fmaf(As[j * Lc], gs[w & 0x7ffu], acc);
+    if (w & kSlotEnd) {
+      os[(w >> 11) & 0x7ffu] = acc;
       acc = 0.0f;
     }
   }

@@ -48,21 +48,23 @@ __device__ __forceinline__ void solve_group(const WarpArgs &a, int g,
   double *dvs = rhs + a.segV;    // Jacobi reciprocals
   const int c = g * a.k + seg;
   const bool has = c < a.cells;
-  // ---- stage the cell's matrix values (Sec. 3.1: one cell, one team)
-  const double *As;
+#define SPMV(out)                                                    \
+  do {                                                               \
+    if (ASMEM) seg_spmv(sch, a.L, Lc, Asl, gs, out);                 \
+    else seg_spmv_gather(sch, srcl, a.L, Lc, Ac, gs, out);           \
+  } while (0)
+  // ---- stage the cell's matrix values in slot order (Sec. 3.1: one cell,
+  // one team); the transposed view's permutation is folded into src
+  const double *Ac = a.A + (size_t)(has ? c : 0) * nnz;
+  const int *srcl = a.src + sl;
+  const int LL = a.L * Lc;
   if (ASMEM) {
-    if (has) {
-      const double *Ac = a.A + (size_t)c * nnz;
-      if (a.a_perm) {
-        for (int k = sl; k < nnz; k += Lc) Abase[k] = __ldg(Ac + __ldg(a.a_perm + k));
-      } else {
-        for (int k = sl; k < nnz; k += Lc) Abase[k] = __ldg(Ac + k);
-      }
-    }
-    As = Abase;
-  } else {
-    As = a.A + (size_t)(has ? c : 0) * nnz;   // read through L1
+    // coalesced read of the cell's A row, scattered into slot order; each lane
+    // zeroes its own padding slots (never a scatter target)
+    for (int k = sl; k < nnz; k += Lc) Abase[__ldg(a.dst + k)] = has ? __ldg(Ac + k) : 0.0;
+    for (int t = __ldg(a.padfrom + sl) * Lc + sl; t < LL; t += Lc) Abase[t] = 0.0;
   }
+  const double *Asl = Abase + sl;  // this lane's slots (stride Lc)
   // pad rows of the product vectors are never written by the SpMV
   for (int i = n + sl; i < E * Lc; i += Lc) {
     o1[i] = 0.0;
@@ -79,7 +81,8 @@ __device__ __forceinline__ void solve_group(const WarpArgs &a, int g,
       const int i = sl + e * Lc;
       const bool v = has && i < n;
       const double bi = v ? __ldg(a.b + (size_t)c * n + i) : 0.0;
-      const double d = v ? As[__ldg(a.diag + i)] : 0.0;
+      const double d = v ? (ASMEM ? Abase[__ldg(a.dslot + i)]
+                               : __ldg(Ac + __ldg(a.src + __ldg(a.dslot + i)))) : 0.0;
       dvs[i] = v ? (!is_zero_bits(d) ? recip64(d) : 1.0) : 0.0;
       xv[e] = (v && a.x0_given) ? a.x[(size_t)c * n + i] : 0.0;
       r[e] = bi;
@@ -110,7 +113,7 @@ __device__ __forceinline__ void solve_group(const WarpArgs &a, int g,
 #pragma unroll
     for (int e = 0; e < E; ++e) gs[sl + e * Lc] = xv[e];
     __syncwarp();
-    seg_spmv(sch, a.L, Lc, As, gs, o1);
+    SPMV(o1);
     __syncwarp();
 #pragma unroll
     for (int e = 0; e < E; ++e) r[e] -= o1[sl + e * Lc];
@@ -162,7 +165,7 @@ __device__ __forceinline__ void solve_group(const WarpArgs &a, int g,
         gs[i] = dvs[i] * p[e];
       }
       __syncwarp();
-      seg_spmv(sch, a.L, Lc, As, gs, o1);  // v = A p^
+      SPMV(o1);  // v = A p^
       __syncwarp();
       if (active) ++it;
       double sg[1] = {0.0};
@@ -193,7 +196,7 @@ __device__ __forceinline__ void solve_group(const WarpArgs &a, int g,
         gs[i] = dvs[i] * s[e];
       }
       __syncwarp();
-      seg_spmv(sch, a.L, Lc, As, gs, o2);  // t = A s^
+      SPMV(o2);  // t = A s^
       __syncwarp();
       double q0 = 0.0, q1 = 0.0, q2 = 0.0;
 #pragma unroll
@@ -253,7 +256,7 @@ __device__ __forceinline__ void solve_group(const WarpArgs &a, int g,
 #pragma unroll
     for (int e = 0; e < E; ++e) gs[sl + e * Lc] = xv[e];
     __syncwarp();
-    seg_spmv(sch, a.L, Lc, As, gs, o1);
+    SPMV(o1);
     __syncwarp();
     double rt2[1] = {0.0};
 #pragma unroll
@@ -297,6 +300,7 @@ __device__ __forceinline__ void solve_group(const WarpArgs &a, int g,
     }
   }
   __syncwarp();
+#undef SPMV
 }
 
 // Plain launch: one mechanism, the SpMV schedule in shared memory, groups of
@@ -311,7 +315,7 @@ __global__ void __launch_bounds__(256, CAMP_WARP_MINB)
   __syncthreads();
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
-  double *wbase = reinterpret_cast<double *>(smem_raw + (((size_t)nsch * 8 + 15) & ~(size_t)15)) +
+  double *wbase = reinterpret_cast<double *>(smem_raw + sched_smem_bytes(nsch)) +
                   (size_t)warp * a.k * a.segStride;
   const SchedWord *sch = sch_s + (lane & (a.Lc - 1));
   const int warps_total = gridDim.x * (blockDim.x >> 5);

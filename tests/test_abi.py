@@ -128,16 +128,18 @@ def test_spmv_schedule_replays_the_product(lib, wid):
         for lane in range(lc):
             acc = 0.0
             for j in range(L.value):
-                w0, w1 = int(w[j, lane, 0]), int(w[j, lane, 1])
-                k, col = w0 & 0xFFFF, w0 >> 16
-                acc += vals[k] * x[col]
-                if w1 >> 16:
-                    row = w1 & 0xFFFF
+                src, w1 = int(w[j, lane, 0]), int(w[j, lane, 1])
+                col = w1 & 0x7FF
+                if src != 0xFFFFFFFF:
+                    acc += vals[src] * x[col]
+                    used[src] += 1
+                    assert col == m.col_idx[src]
+                if w1 >> 31:
+                    row = (w1 >> 11) & 0x7FF
                     assert np.isnan(y[row])
                     y[row] = acc
                     acc = 0.0
-                    used[m.row_ptr[row]:m.row_ptr[row + 1]] += 1
-                    assert col == m.col_idx[k] and k == m.row_ptr[row + 1] - 1
+                    assert src == m.row_ptr[row + 1] - 1
         assert np.all(used == 1)
         np.testing.assert_allclose(y, y_ref, rtol=1e-13, atol=1e-13 * np.abs(y_ref).max())
         # balance: no lane exceeds the mean by more than the longest row
