@@ -163,6 +163,23 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def max_over_ranks(value: float, device=None) -> float:
+    """Max of a per-rank float over all ranks (the job's time is its slowest
+    rank's); identity without torch.distributed."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(value)
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def weak_value(world: int, cells: int, steps: int, total_ms: float) -> float:
+    """Whole-job throughput: every rank solves its own `cells` per step."""
+    return world * cells * steps / (total_ms * 1e-3)
+
+
 def set_arrangement(camp, solver, spec):
     parts = spec.split(":")
     if parts[0] == "auto":
@@ -218,11 +235,7 @@ def time_e2e(camp, solver, cb, C, tol, maxit, steps, world, dev):
     t0 = time.perf_counter()
     for _ in range(steps):
         camp.camp_solver_solve_host(solver.h, C, hA, hb, hx, tol, maxit, hit, hres, hst)
-    el = time.perf_counter() - t0
-    if world > 1:
-        t = torch.tensor([el], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        el = float(t.item())
+    el = max_over_ranks(time.perf_counter() - t0, dev)
     return {"value": world * C * steps / el, "unit": UNIT,
             "h2d_bytes_per_step": C * (m.nnz + m.n) * 8,
             "d2h_bytes_per_step": C * (m.n * 8 + 4 + 8 + 4)}
@@ -342,15 +355,11 @@ def main():
     if world > 1:
         dist.barrier()
     clk = clocks.stop()
-    total_ms = float(sum(times))
-    if world > 1:
-        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(float(sum(times)), dev)
     iters = it.cpu().numpy()
     status = st.cpu().numpy()
     sw = sweeps.cpu().numpy()
-    value = world * C * args.steps / (total_ms * 1e-3)
+    value = weak_value(world, C, args.steps, total_ms)
     ms_step = total_ms / args.steps
     kernel_s = ms_step * 1e-3
     hbm_peak, hbm_src = peaks()

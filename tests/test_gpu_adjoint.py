@@ -92,3 +92,42 @@ def test_solve_host_equals_device(cuda):
     np.testing.assert_array_equal(hr.numpy(), rd.cpu().numpy())
     np.testing.assert_array_equal(hs.numpy(), sd.cpu().numpy())
     s.close()
+
+
+def test_adjoint_full_size_sampled(cuda):
+    """Adjoint workload at full size (80 species, 10000 cells, tol 1e-10): the
+    gradients of L = sum_c w_c . x_c from the autograd Function on 16 sampled
+    cells against dense LAPACK gradients and central differences (step 1e-6,
+    dense forward solves)."""
+    import torch
+    from paper_2405_17363_gb300 import camp
+    cbs, tol, maxit = synth.workload(3)
+    cb = cbs[0]
+    m = cb.mech
+    w = np.random.default_rng(3000).standard_normal((cb.cells, m.n))
+    s = camp.Solver(m.row_ptr, m.col_idx)
+    A = torch.as_tensor(cb.A_vals, device=cuda).requires_grad_(True)
+    b = torch.as_tensor(cb.b, device=cuda).requires_grad_(True)
+    x, it, res, st = camp.solve(A, b, s, tol, maxit)
+    (x * torch.as_tensor(w, device=cuda)).sum().backward()
+    assert int((st == 0).sum()) == cb.cells
+    gA = A.grad.cpu().numpy()
+    gb = b.grad.cpu().numpy()
+    rows = np.repeat(np.arange(m.n), np.diff(m.row_ptr))
+    rng = np.random.default_rng(16)
+    for c in rng.choice(cb.cells, 16, replace=False):
+        Ad = m.dense(cb.A_vals[c])
+        lam = np.linalg.solve(Ad.T, w[c])
+        xd = np.linalg.solve(Ad, cb.b[c])
+        kappa = np.linalg.cond(Ad, 1)
+        bar = max(1e-8, 4 * kappa * tol)
+        assert np.linalg.norm(gb[c] - lam) <= bar * np.linalg.norm(lam)
+        g_ref = -lam[rows] * xd[m.col_idx]
+        assert np.linalg.norm(gA[c] - g_ref) <= bar * np.linalg.norm(g_ref)
+        for k in rng.choice(m.nnz, 3, replace=False):
+            h = 1e-6 * max(1.0, abs(cb.A_vals[c, k]))
+            Ap = Ad.copy(); Ap[rows[k], m.col_idx[k]] += h
+            Am = Ad.copy(); Am[rows[k], m.col_idx[k]] -= h
+            fd = (w[c] @ np.linalg.solve(Ap, cb.b[c]) - w[c] @ np.linalg.solve(Am, cb.b[c])) / (2 * h)
+            assert abs(fd - gA[c, k]) <= 1e-6 * max(1.0, abs(fd))
+    s.close()

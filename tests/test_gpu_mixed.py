@@ -40,3 +40,37 @@ def test_mixed_matches_fp64_oracle(cuda, wid, cells):
     print(f"mixed wid{wid}: error vs FP64 oracle max {err.max():.2e} p99 "
           f"{np.percentile(err, 99):.2e}; sweeps mean {sweeps.mean():.2f}")
     s.close()
+
+
+def test_mixed_full_size_sampled(cuda):
+    """Mixed-precision workload at full size (150 species, 100000 cells): every
+    cell's FP64 true residual on the host, 200 sampled cells against the FP64
+    oracle and the refinement oracle; error against FP64 reported."""
+    import torch
+    from paper_2405_17363_gb300 import camp
+    cbs, tol, maxit = synth.workload(4)
+    cb = cbs[0]
+    m = cb.mech
+    s = camp.Solver(m.row_ptr, m.col_idx)
+    A = torch.as_tensor(cb.A_vals, device=cuda)
+    b = torch.as_tensor(cb.b, device=cuda)
+    x, it, sw, res, st = s.solve_mixed(A, b, tol)
+    torch.cuda.synchronize()
+    X = x.cpu().numpy()
+    status = st.cpu().numpy()
+    sweeps = sw.cpu().numpy()
+    assert np.all(status == 0)
+    for lo in range(0, cb.cells, 20000):
+        hi = lo + 20000
+        r = parity.true_resid(m, cb.A_vals[lo:hi], X[lo:hi], cb.b[lo:hi])
+        assert np.all(r <= tol * 1.0001)
+    idx = np.unique(np.r_[0, np.random.default_rng(4).choice(cb.cells, 198, replace=False), cb.cells - 1])
+    f64 = oracle.solve(m.row_ptr, m.col_idx, cb.A_vals[idx], cb.b[idx], tol, maxit, threads=8)
+    mix = oracle.solve_mixed(m.row_ptr, m.col_idx, cb.A_vals[idx], cb.b[idx], tol, threads=8)
+    assert np.all(np.abs(sweeps[idx] - mix["sweeps"]) <= 1)
+    gpu = dict(x=X[idx], iters=f64["iters"], resid=res.cpu().numpy()[idx], status=status[idx])
+    parity.compare(m, cb.A_vals[idx], cb.b[idx], tol, gpu, f64, "mixed full")
+    err = np.linalg.norm(X[idx] - f64["x"], axis=1) / np.linalg.norm(f64["x"], axis=1)
+    print(f"mixed 150 sp x 100000 cells: error vs FP64 oracle max {err.max():.2e} "
+          f"p99 {np.percentile(err, 99):.2e}")
+    s.close()
