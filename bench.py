@@ -282,6 +282,43 @@ def run_uneven_case(args):
     print(json.dumps({"case": "uneven", **res}), flush=True)
 
 
+def run_arrangements_case(args):
+    """--case arrangements: the paper's kernel-configuration study (Sec. 3.2,
+    Sec. 5.2) on the headline workload: every arrangement's solve time and
+    iterations, per-cell scalars and coupled (shared-scalar) Block-cells(k)."""
+    import torch
+    from paper_2405_17363_gb300 import camp
+    dev = torch.device("cuda", 0)
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+    cbs, tol, maxit = synth.workload(WORKLOAD_ID)
+    cb = cbs[0]
+    m = cb.mech
+    s = camp.Solver(m.row_ptr, m.col_idx)
+    A = torch.as_tensor(cb.A_vals, device=dev)
+    b = torch.as_tensor(cb.b, device=dev)
+    nmax = 1024 // m.n
+    arrs = [("warp-packed auto", (camp.CAMP_ARR_AUTO, 0, 1, 0)),
+            ("warp per cell (32 lanes)", (camp.CAMP_ARR_WARP, 32, 0, 0))]
+    for cpb in (1, 2, 3, nmax):
+        arrs.append((f"Block-cells({cpb}) per-cell scalars", (camp.CAMP_ARR_BLOCK, 0, cpb, 0)))
+    for cpb in (2, 3, nmax):
+        arrs.append((f"Block-cells({cpb}) coupled", (camp.CAMP_ARR_BLOCK_COUPLED, 0, cpb, 0)))
+    rows = []
+    for name, arr in arrs:
+        s.set_arrangement(*arr)
+        out = s.solve(A, b, tol, maxit)
+        ms = sum(time_steps(lambda: s.solve(A, b, tol, maxit, out=out), flush, stream,
+                            args.steps, 3)) / args.steps
+        it = out[1].cpu().numpy()
+        rows.append({"arrangement": name, "ms": ms, "value": cb.cells / (ms * 1e-3),
+                     "iters_mean": float(it.mean()), "iters_max": int(it.max()),
+                     "converged": int((out[3] == 0).sum().item())})
+    s.close()
+    print(json.dumps({"case": "arrangements", "workload": synth.WORKLOADS[WORKLOAD_ID][0],
+                      "unit": UNIT, "rows": rows}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -294,7 +331,7 @@ def main():
                     help="auto | warp:<lanes per cell>[:<warps per block>] | block:<cells per block>")
     ap.add_argument("--mode", default="fp64", choices=["fp64", "mixed"],
                     help="fp64: plain FP64 solve (the headline); mixed: FP32-inner refinement")
-    ap.add_argument("--case", default="headline", choices=["headline", "uneven"],
+    ap.add_argument("--case", default="headline", choices=["headline", "uneven", "arrangements"],
                     help="headline: the 80-species 10k-cell FP64 solve; uneven: time the "
                          "persistent multi-mechanism batch as the step (for profiling)")
     ap.add_argument("--skip-extras", action="store_true",
@@ -311,6 +348,8 @@ def main():
         return run_reference(args, rank, world)
     if args.case == "uneven":
         return run_uneven_case(args)
+    if args.case == "arrangements":
+        return run_arrangements_case(args)
 
     import torch
     import torch.distributed as dist

@@ -75,7 +75,8 @@ enum {
 enum {
   CAMP_ARR_AUTO = 0,  /* library choice (tuned table or heuristic) */
   CAMP_ARR_WARP = 1,  /* 32/lanes_per_cell cells per warp, one warp per group */
-  CAMP_ARR_BLOCK = 2  /* cells_per_block cells per CTA, one thread per row */
+  CAMP_ARR_BLOCK = 2, /* cells_per_block cells per CTA, one thread per row */
+  CAMP_ARR_BLOCK_COUPLED = 3 /* as BLOCK, but the CTA's cells form one system */
 };
 
 /*
@@ -105,6 +106,14 @@ camp_status camp_solver_set_stream(camp_solver_t h, void *stream);
  *                   lanes_per_cell = 32 is "warp per cell".
  *   CAMP_ARR_BLOCK: cells_per_block cells per CTA with one thread per row
  *                   (cells_per_block = 1 is the paper's Block-cells(1)).
+ *   CAMP_ARR_BLOCK_COUPLED: the paper's Block-cells(k) semantics (Sec. 3.2):
+ *                   the cells of a CTA share the BiCGSTAB scalars and one
+ *                   convergence test, i.e. they are solved as one
+ *                   block-diagonal system; tol applies to the block's
+ *                   combined residual ||b - A x|| / ||b||, and iters, resid
+ *                   and status are the block's, written to each of its
+ *                   cells.  Cells are grouped in index order, cells_per_block
+ *                   per CTA (the last CTA takes the remainder).
  *   CAMP_ARR_AUTO : library choice.
  * Unused arguments are ignored.  Returns CAMP_EINVAL for unsupported values.
  */

@@ -27,7 +27,7 @@ CAMP_OK, CAMP_EINVAL, CAMP_ECUDA, CAMP_ENOMEM, CAMP_EPATTERN, CAMP_EUNSUPPORTED 
 CAMP_CELL_CONVERGED, CAMP_CELL_MAXIT, CAMP_CELL_BREAKDOWN, CAMP_CELL_NONFINITE = \
     0, 1, 2, 3
 CAMP_TRANSPOSE, CAMP_X0_GIVEN = 1, 2
-CAMP_ARR_AUTO, CAMP_ARR_WARP, CAMP_ARR_BLOCK = 0, 1, 2
+CAMP_ARR_AUTO, CAMP_ARR_WARP, CAMP_ARR_BLOCK, CAMP_ARR_BLOCK_COUPLED = 0, 1, 2, 3
 
 _P = ctypes.c_void_p
 _I = ctypes.c_int

@@ -60,6 +60,36 @@ __device__ __forceinline__ void cell_sum(double (&v)[NV], double *prod,
   for (int q = 0; q < NV; ++q) v[q] = in_block ? tot[q * cpb + j] : 0.0;
 }
 
+// Coupled mode (the paper's Block-cells(N) semantics, Sec. 3.2): one total
+// over every row of the block's present cells, i.e. the cells of a block form
+// one block-diagonal system with shared scalars and one convergence test.
+// Warp shuffles, one partial per warp in shared memory, warp 0 sums them.
+template <int NV>
+__device__ __forceinline__ void block_total(double (&v)[NV], double *prod,
+                                            double *tot, bool contrib) {
+  const int t = threadIdx.x, lane = t & 31, w = t >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int q = 0; q < NV; ++q) {
+    double acc = contrib ? v[q] : 0.0;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(kFullB, acc, off);
+    if (lane == 0) prod[q * 32 + w] = acc;
+  }
+  __syncthreads();
+  if (w == 0) {
+#pragma unroll
+    for (int q = 0; q < NV; ++q) {
+      double acc = lane < nw ? prod[q * 32 + lane] : 0.0;
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(kFullB, acc, off);
+      if (lane == 0) tot[q] = acc;
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int q = 0; q < NV; ++q) v[q] = tot[q];
+}
+
 }  // namespace
 
 __global__ void __launch_bounds__(1024) block_bicgstab_kernel(const BlockArgs a) {
@@ -118,7 +148,8 @@ __global__ void __launch_bounds__(1024) block_bicgstab_kernel(const BlockArgs a)
   };
 
   double bbv[1] = {bi * bi};
-  cell_sum<1>(bbv, prod, tot, n, cpb, j, in_block);
+  if (a.coupled) block_total<1>(bbv, prod, tot, has);
+      else cell_sum<1>(bbv, prod, tot, n, cpb, j, in_block);
   const double bb = bbv[0];
   const double bnorm = sqrt(bb);
   const double thr = (a.tol * bnorm) * (a.tol * bnorm);
@@ -150,7 +181,8 @@ __global__ void __launch_bounds__(1024) block_bicgstab_kernel(const BlockArgs a)
   for (;;) {
     {
       double rr[1] = {r * r};
-      cell_sum<1>(rr, prod, tot, n, cpb, j, in_block);
+      if (a.coupled) block_total<1>(rr, prod, tot, has);
+      else cell_sum<1>(rr, prod, tot, n, cpb, j, in_block);
       if (restart) {
         rh = r;
         p = 0.0;
@@ -186,7 +218,8 @@ __global__ void __launch_bounds__(1024) block_bicgstab_kernel(const BlockArgs a)
       if (active) ++it;
       const double v = in_block ? v1[i] : 0.0;
       double sg[1] = {rh * v};
-      cell_sum<1>(sg, prod, tot, n, cpb, j, in_block);
+      if (a.coupled) block_total<1>(sg, prod, tot, has);
+      else cell_sum<1>(sg, prod, tot, n, cpb, j, in_block);
       if (active) {
         if (!fin_bits(sg[0])) {
           nonfin = true;
@@ -209,7 +242,8 @@ __global__ void __launch_bounds__(1024) block_bicgstab_kernel(const BlockArgs a)
       __syncthreads();
       const double tv = in_block ? v2[i] : 0.0;
       double q3[3] = {s * s, tv * s, tv * tv};
-      cell_sum<3>(q3, prod, tot, n, cpb, j, in_block);
+      if (a.coupled) block_total<3>(q3, prod, tot, has);
+      else cell_sum<3>(q3, prod, tot, n, cpb, j, in_block);
       bool full = false;
       if (active) {
         if (le_nn(q3[0], thr)) {
@@ -232,7 +266,8 @@ __global__ void __launch_bounds__(1024) block_bicgstab_kernel(const BlockArgs a)
         p = fma(-om, v, p);
       }
       double q2[2] = {rh * r, r * r};
-      cell_sum<2>(q2, prod, tot, n, cpb, j, in_block);
+      if (a.coupled) block_total<2>(q2, prod, tot, has);
+      else cell_sum<2>(q2, prod, tot, n, cpb, j, in_block);
       if (full) {
         nbreak = 0;
         if (le_nn(q2[1], thr)) {
@@ -253,7 +288,8 @@ __global__ void __launch_bounds__(1024) block_bicgstab_kernel(const BlockArgs a)
     __syncthreads();
     const double rt = bi - (in_block ? v1[i] : 0.0);
     double rt2[1] = {rt * rt};
-    cell_sum<1>(rt2, prod, tot, n, cpb, j, in_block);
+    if (a.coupled) block_total<1>(rt2, prod, tot, has);
+      else cell_sum<1>(rt2, prod, tot, n, cpb, j, in_block);
     if (fin) {
       fin = false;
       resid = sqrt(rt2[0]) / bnorm;

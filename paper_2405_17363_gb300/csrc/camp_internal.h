@@ -80,6 +80,7 @@ struct BlockArgs {
   double tol;
   int maxit;
   int x0_given;
+  int coupled;  // 1: the block's cells form one system (shared scalars, one test)
 };
 
 // per-cell grad kernel arguments

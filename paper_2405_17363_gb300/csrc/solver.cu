@@ -363,6 +363,7 @@ camp_status do_solve(camp_solver_t h, int cells, const double *A_vals,
   a.status = status_out; a.a_perm = v.d_perm; a.diag = v.d_diag;
   a.row_ptr = v.d_rp; a.col_idx = v.d_ci; a.tol = tol; a.maxit = maxit;
   a.x0_given = (flags & CAMP_X0_GIVEN) ? 1 : 0;
+  a.coupled = (arr == CAMP_ARR_BLOCK_COUPLED) ? 1 : 0;
   e = launch_block(a, threads, smem, st);
   if (e != cudaSuccess) return cuda_fail(e, "block kernel launch");
   return CAMP_OK;
@@ -529,7 +530,7 @@ camp_status camp_solver_set_arrangement(camp_solver_t h, int arrangement,
     h->wpb = warps_per_block;
     return CAMP_OK;
   }
-  if (arrangement == CAMP_ARR_BLOCK) {
+  if (arrangement == CAMP_ARR_BLOCK || arrangement == CAMP_ARR_BLOCK_COUPLED) {
     if (cells_per_block < 1 || cells_per_block * h->n > 1024)
       return fail(CAMP_EINVAL, "cells_per_block*n must be in [n, 1024]");
     h->arrangement = arrangement;

@@ -49,3 +49,15 @@ def true_resid(mech, A_vals, x, b):
     prod = A_vals * x[:, mech.col_idx]
     np.add.at(Ax, (slice(None), rows), prod)
     return np.linalg.norm(b - Ax, axis=1) / np.linalg.norm(b, axis=1)
+
+
+def block_diagonal(mech, A_vals, b, c0, k):
+    """The cells c0 .. c0+k-1 as one block-diagonal system (the coupled
+    Block-cells(k) reading): CSR (row_ptr, col_idx), values [1, k*nnz] and
+    right-hand side [1, k*n]."""
+    n, nnz = mech.n, mech.nnz
+    rp = np.concatenate([[0]] + [mech.row_ptr[1:] + j * nnz for j in range(k)]).astype(np.int32)
+    ci = np.concatenate([mech.col_idx + j * n for j in range(k)]).astype(np.int32)
+    vals = np.ascontiguousarray(A_vals[c0:c0 + k].reshape(1, k * nnz))
+    rhs = np.ascontiguousarray(b[c0:c0 + k].reshape(1, k * n))
+    return rp, ci, vals, rhs
