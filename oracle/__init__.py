@@ -58,6 +58,8 @@ def _load():
                                             P, P, P, I]
             lib.orc_transpose_pattern.restype = None
             lib.orc_transpose_pattern.argtypes = [I, P, P, P, P, P]
+            lib.orc_assemble_cell.restype = I
+            lib.orc_assemble_cell.argtypes = [I, P, P, I, P, P, P, P, P, D, P]
             lib.orc_grad_A_cell.restype = None
             lib.orc_grad_A_cell.argtypes = [I, P, P, P, P, P]
             _lib = lib
@@ -133,6 +135,27 @@ def transpose_pattern(row_ptr, col_idx):
     src = np.zeros(nnz, dtype=np.int32)
     lib.orc_transpose_pattern(n, _p(rp), _p(ci), _p(rpt), _p(cit), _p(src))
     return rpt, cit, src
+
+
+def assemble(row_ptr, col_idx, reactant_a, reactant_b, product, k, conc, gamma):
+    """A_vals [cells, nnz] = I - gamma_c J(conc_c) on the pattern (mass action;
+    reactant_b = -1 marks a first-order reaction)."""
+    lib = _load()
+    rp, ci = _i32(row_ptr), _i32(col_idx)
+    ra, rb, pr = _i32(reactant_a), _i32(reactant_b), _i32(product)
+    kk = _f64(k)
+    C = _f64(np.atleast_2d(conc))
+    g = _f64(np.atleast_1d(gamma))
+    cells, n = C.shape
+    nnz = int(rp[-1])
+    A = np.zeros((cells, nnz))
+    for c in range(cells):
+        code = lib.orc_assemble_cell(n, _p(rp), _p(ci), int(ra.shape[0]), _p(ra), _p(rb),
+                                     _p(pr), _p(kk), _p(np.ascontiguousarray(C[c])),
+                                     float(g[c]), _p(A[c]))
+        if code != 0:
+            raise ValueError("a Jacobian entry lies outside the pattern")
+    return A
 
 
 def adjoint(row_ptr, col_idx, A_vals, x, w, tol=1e-10, maxit=500, threads=1):

@@ -412,3 +412,57 @@ int orc_mixed_batch(int cells, int n, int nnz, const int *rp, const int *ci,
   int used = run_batch(&B, nthreads);
   return used > 0 ? used : 1;
 }
+
+/* ---- mass-action Jacobian assembly (the step before the solve) --------- */
+
+/* Position of (row i, column j) in the CSR pattern, or -1. */
+static int csr_pos(const int *rp, const int *ci, int i, int j) {
+  for (int k = rp[i]; k < rp[i + 1]; ++k)
+    if (ci[k] == j) return k;
+  return -1;
+}
+
+/*
+ * A = I - gamma J(conc) for one cell on the CSR pattern, J the mass-action
+ * Jacobian of R reactions: reaction r consumes ra[r] (and rb[r] when
+ * rb[r] >= 0) and produces pr[r] at rate k[r] y_a (first order) or
+ * k[r] y_a y_b (second order), so dy_i/dt sums -rate over consumed and +rate
+ * over produced species (the paper's f_i = sum_j (dy_i/dt)_j, Sec. 2.2) and J
+ * is its derivative in y.  J is accumulated in reaction order, each term a
+ * separately rounded product and sum.  Returns 0, or -1 if a Jacobian entry
+ * falls outside the pattern.
+ */
+int orc_assemble_cell(int n, const int *rp, const int *ci, int R,
+                      const int *ra, const int *rb, const int *pr,
+                      const double *k, const double *conc, double gamma,
+                      double *A) {
+  int nnz = rp[n];
+  for (int q = 0; q < nnz; ++q) A[q] = 0.0; /* J accumulates here first */
+  for (int r = 0; r < R; ++r) {
+    const int a = ra[r], b = rb[r], c = pr[r];
+    if (b < 0) {
+      /* rate = k y_a: d/dy_a of -rate (row a) and +rate (row c) */
+      int p1 = csr_pos(rp, ci, a, a), p2 = csr_pos(rp, ci, c, a);
+      if (p1 < 0 || p2 < 0) return -1;
+      A[p1] = A[p1] - k[r];
+      A[p2] = A[p2] + k[r];
+    } else {
+      /* rate = k y_a y_b: d/dy_a = k y_b, d/dy_b = k y_a; rows a, b lose, c gains */
+      const double da = k[r] * conc[b], db = k[r] * conc[a];
+      int paa = csr_pos(rp, ci, a, a), pab = csr_pos(rp, ci, a, b);
+      int pba = csr_pos(rp, ci, b, a), pbb = csr_pos(rp, ci, b, b);
+      int pca = csr_pos(rp, ci, c, a), pcb = csr_pos(rp, ci, c, b);
+      if (paa < 0 || pab < 0 || pba < 0 || pbb < 0 || pca < 0 || pcb < 0) return -1;
+      A[paa] = A[paa] - da;
+      A[pab] = A[pab] - db;
+      A[pba] = A[pba] - da;
+      A[pbb] = A[pbb] - db;
+      A[pca] = A[pca] + da;
+      A[pcb] = A[pcb] + db;
+    }
+  }
+  for (int i = 0; i < n; ++i)
+    for (int q = rp[i]; q < rp[i + 1]; ++q)
+      A[q] = ((ci[q] == i) ? 1.0 : 0.0) - gamma * A[q];
+  return 0;
+}

@@ -402,3 +402,31 @@ def test_initial_guess_iteration_counts_equal_scipy():
         assert info == 0
         assert out["iters"][c] == it, (c, out["iters"][c], it)
         np.testing.assert_allclose(out["x"][c], xs, rtol=1e-9, atol=1e-9 * np.abs(xs).max())
+
+
+def test_assembly_matches_independent_numpy_jacobian():
+    """The oracle's C mass-action assembly against the generator's NumPy one
+    (itself pinned by Euler's identity and finite differences of the rates):
+    two codings of the same Jacobian agree to rounding."""
+    for wid in (0, 1, 4):
+        cbs, _, _ = synth.workload(wid, cells=12)
+        cb = cbs[0]
+        m = cb.mech
+        A = oracle.assemble(m.row_ptr, m.col_idx, m.reactants[:, 0], m.reactants[:, 1],
+                            m.products, m.k, cb.conc, cb.gamma)
+        scale = np.abs(cb.A_vals).max(axis=1, keepdims=True)
+        assert np.all(np.abs(A - cb.A_vals) <= 1e-15 * scale)
+
+
+def test_assembly_rejects_entries_outside_the_pattern():
+    m = synth.make_mechanism(8, 6, 3)
+    # drop one off-diagonal coupling from the pattern
+    rows = np.repeat(np.arange(m.n), np.diff(m.row_ptr))
+    k = int(np.nonzero(rows != m.col_idx)[0][0])
+    keep = np.ones(m.nnz, bool)
+    keep[k] = False
+    ci = m.col_idx[keep]
+    rp = np.r_[0, np.cumsum(np.bincount(rows[keep], minlength=m.n))].astype(np.int32)
+    with pytest.raises(ValueError):
+        oracle.assemble(rp, ci, m.reactants[:, 0], m.reactants[:, 1], m.products, m.k,
+                        np.ones((1, m.n)), [0.1])
