@@ -274,6 +274,37 @@ camp_status camp_schedule_build(int n, int nnz, const int *row_ptr,
                                 unsigned *words, int capacity_slots,
                                 int *slots_per_lane);
 
+/*
+ * Fused Jacobian assembly.  The matrix of each cell is the Newton matrix of
+ * the BDF step, A = I - gamma J, J the Jacobian of the species rates
+ * f_i = sum_j (dy_i/dt)_j of the mechanism (Sec. 2.2).  For a mass-action
+ * mechanism the kernel can build A for every cell in shared memory from the
+ * cell's concentrations instead of reading A_vals from HBM.
+ *
+ * camp_solver_set_mechanism attaches R reactions (HOST arrays [R]): reaction
+ * r consumes reactant_a[r] and, when reactant_b[r] >= 0, reactant_b[r], and
+ * produces product[r], at rate rate_k[r] y_a (first order, reactant_b = -1)
+ * or rate_k[r] y_a y_b (second order); rate constants are shared by all
+ * cells.  Every Jacobian entry the reactions create must be in the handle's
+ * pattern (else CAMP_EPATTERN).  Replaces any earlier mechanism.
+ *
+ * camp_solver_assemble_solve then solves, for every cell,
+ * (I - gamma[c] J(conc[c])) x = b[c] exactly as camp_solver_solve_ex would
+ * with those matrix values: conc [cells x n], gamma [cells], b, x [cells x n],
+ * iters_out, resid_out, status_out (may be NULL) [cells], device pointers.
+ * At most 8 rows per lane of the warp arrangement (n <= 256).
+ */
+camp_status camp_solver_set_mechanism(camp_solver_t h, int R,
+                                      const int *reactant_a,
+                                      const int *reactant_b,
+                                      const int *product,
+                                      const double *rate_k);
+camp_status camp_solver_assemble_solve(camp_solver_t h, int cells,
+                                       const double *conc, const double *gamma,
+                                       const double *b, double *x, double tol,
+                                       int maxit, int *iters_out,
+                                       double *resid_out, int *status_out);
+
 /* Thread-local message describing the last error (never NULL). */
 const char *camp_last_error(void);
 

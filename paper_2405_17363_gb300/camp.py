@@ -51,6 +51,8 @@ _grad_A = _sig("camp_solver_grad_A", [_P, _I, _P, _P, _P])
 _solve_host = _sig("camp_solver_solve_host", [_P, _I, _P, _P, _P, _D, _I, _P, _P, _P])
 _solve_mixed = _sig("camp_solver_solve_mixed",
                     [_P, _I, _P, _P, _P, _D, _I, _D, _I, _P, _P, _P, _P])
+_set_mech = _sig("camp_solver_set_mechanism", [_P, _I, _P, _P, _P, _P])
+_assemble_solve = _sig("camp_solver_assemble_solve", [_P, _I, _P, _P, _P, _P, _D, _I, _P, _P, _P])
 _batch_create = _sig("camp_batch_create", [ctypes.POINTER(_P), _I, _P])
 _batch_destroy = _sig("camp_batch_destroy", [_P])
 _batch_set_stream = _sig("camp_batch_set_stream", [_P, _P])
@@ -189,6 +191,30 @@ def camp_solver_solve_mixed(h, cells, A_vals, b, x, tol, max_sweeps, tol_inner,
            "camp_solver_solve_mixed")
 
 
+def camp_solver_set_mechanism(h, reactant_a, reactant_b, product, rate_k):
+    """Attach a mass-action mechanism (host arrays [R]; reactant_b = -1 for
+    first-order reactions) for camp_solver_assemble_solve."""
+    import numpy as np
+    ra, pra = _host_i32(reactant_a)
+    rb, prb = _host_i32(reactant_b)
+    pr, ppr = _host_i32(product)
+    k = np.ascontiguousarray(rate_k, dtype=np.float64)
+    _check(_set_mech(h, int(ra.shape[0]), pra, prb, ppr, k.ctypes.data_as(_P)),
+           "camp_solver_set_mechanism")
+
+
+def camp_solver_assemble_solve(h, cells, conc, gamma, b, x, tol, maxit, iters_out,
+                               resid_out, status_out=None):
+    camp_solver_set_stream(h)
+    _check(_assemble_solve(h, int(cells), _dptr(conc, torch.float64, "conc"),
+                           _dptr(gamma, torch.float64, "gamma"), _dptr(b, torch.float64, "b"),
+                           _dptr(x, torch.float64, "x"), float(tol), int(maxit),
+                           _dptr(iters_out, torch.int32, "iters_out"),
+                           _dptr(resid_out, torch.float64, "resid_out"),
+                           _dptr(status_out, torch.int32, "status_out")),
+           "camp_solver_assemble_solve")
+
+
 def camp_batch_create(solver_handles) -> int:
     arr = (_P * len(solver_handles))(*solver_handles)
     h = _P()
@@ -270,6 +296,23 @@ class Solver:
         camp_solver_solve_ex(self.h, cells, A_vals, b, x, tol, maxit, iters, resid,
                              status, flags)
         return x, iters, resid, status
+
+    def set_mechanism(self, reactant_a, reactant_b, product, rate_k):
+        camp_solver_set_mechanism(self.h, reactant_a, reactant_b, product, rate_k)
+
+    def assemble_solve(self, conc, gamma, b, tol=1e-10, maxit=500, out=None):
+        """Solve (I - gamma_c J(conc_c)) x_c = b_c with the matrices built in the
+        kernel; returns (x, iters, resid, status)."""
+        cells = b.shape[0]
+        dev = b.device
+        if out is None:
+            out = (torch.empty((cells, self.n), dtype=torch.float64, device=dev),
+                   torch.empty(cells, dtype=torch.int32, device=dev),
+                   torch.empty(cells, dtype=torch.float64, device=dev),
+                   torch.empty(cells, dtype=torch.int32, device=dev))
+        camp_solver_assemble_solve(self.h, cells, conc, gamma, b, out[0], tol, maxit,
+                                   out[1], out[2], out[3])
+        return out
 
     def grad_A(self, lam, x, out=None):
         gA = out if out is not None else torch.empty(

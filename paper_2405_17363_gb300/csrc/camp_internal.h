@@ -50,6 +50,15 @@ struct WarpArgs {
   // finished.  The last warp to finish resets both to zero, so the pair is
   // ready for the next launch in stream order.  Null: static assignment.
   unsigned int *queue;
+  // Fused assembly (assemble_bicgstab_kernel only): the cell's matrix is
+  // built in shared memory as A = I - gamma J(conc) instead of read from A:
+  // slot t sums cval[q] * (cspec[q] >= 0 ? conc[cspec[q]] : 1) over
+  // q in [cbeg[t], cbeg[t+1]) (its mass-action terms in reaction order).
+  const double *conc;      // [cells x n]
+  const double *gamma;     // [cells]
+  const int *cbeg;         // [L*Lc + 1]
+  const double *cval;      // [terms] sign * rate constant
+  const int *cspec;        // [terms] species whose concentration multiplies, or -1
 };
 
 // Persistent launch over up to kMaxMech mechanisms: mechanism m owns work
@@ -104,6 +113,10 @@ cudaError_t batch_prepare(int E, bool a_smem, int warps_per_block, size_t smem,
 cudaError_t launch_block(const BlockArgs &a, int threads, size_t smem,
                          cudaStream_t st);
 cudaError_t block_set_smem(size_t smem);
+// fused-assembly solve, E in 1..8
+cudaError_t launch_assemble(int E, const WarpArgs &a, int warps_per_block,
+                            int grid, size_t smem, cudaStream_t st);
+cudaError_t assemble_occupancy(int E, int warps_per_block, size_t smem, int *blocks);
 cudaError_t launch_grad(const GradArgs &a, cudaStream_t st);
 
 constexpr int kMaxE = 16;  // rows per lane supported by the warp kernel

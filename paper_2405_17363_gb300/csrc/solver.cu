@@ -167,6 +167,21 @@ cudaError_t upload(T **dst, const std::vector<T> &src) {
                     cudaMemcpyHostToDevice);
 }
 
+// Mass-action mechanism attached to a handle for the fused assembly: its
+// Jacobian terms in reaction order (pattern entry, concentration factor,
+// signed rate constant) and, per lanes-per-cell choice, the terms grouped by
+// schedule slot on the device.
+struct MechTerms {
+  int *d_cbeg = nullptr, *d_cspec = nullptr;
+  double *d_cval = nullptr;
+};
+struct Mechanism {
+  int R = 0;
+  std::vector<int> entry, spec;
+  std::vector<double> val;
+  std::map<int, MechTerms> by_lanes;
+};
+
 }  // namespace
 }  // namespace camp
 
@@ -190,6 +205,7 @@ struct camp_solver {
   cudaStream_t h_streams[2] = {nullptr, nullptr};
   cudaEvent_t h_ev[4] = {nullptr, nullptr, nullptr, nullptr};
   std::mutex mu;
+  Mechanism mech;
 };
 
 namespace {
@@ -327,7 +343,7 @@ camp_status do_solve(camp_solver_t h, int cells, const double *A_vals,
     }
     if (smem > h->smem_optin)
       return fail(CAMP_EUNSUPPORTED, "cell does not fit in shared memory (%zu bytes)", smem);
-    WarpArgs a;
+    WarpArgs a = {};
     a.cells = cells; a.n = v.n; a.nnz = v.nnz;
     a.Lc = Lc; a.log2Lc = ilog2(Lc); a.k = 32 / Lc; a.L = S->L;
     a.segA = segA; a.segV = segV; a.segStride = segStride;
@@ -357,7 +373,7 @@ camp_status do_solve(camp_solver_t h, int cells, const double *A_vals,
   const size_t smem = block_smem(v.n, v.nnz, cpb, threads);
   if (smem > h->smem_optin)
     return fail(CAMP_EUNSUPPORTED, "block does not fit in shared memory (%zu bytes)", smem);
-  BlockArgs a;
+  BlockArgs a = {};
   a.cells = cells; a.n = v.n; a.nnz = v.nnz; a.cpb = cpb;
   a.A = A_vals; a.b = b; a.x = x; a.iters = iters_out; a.resid = resid_out;
   a.status = status_out; a.a_perm = v.d_perm; a.diag = v.d_diag;
@@ -492,6 +508,11 @@ camp_status camp_solver_destroy(camp_solver_t h) {
   cudaStreamSynchronize(h->stream);
   free_view(h->fwd);
   free_view(h->tr);
+  for (auto &kv : h->mech.by_lanes) {
+    cudaFree(kv.second.d_cbeg);
+    cudaFree(kv.second.d_cspec);
+    cudaFree(kv.second.d_cval);
+  }
   cudaFree(h->d_row_of);
   cudaFree(h->d_queue);
   cudaFree(h->h_dA); cudaFree(h->h_db); cudaFree(h->h_dx);
@@ -652,6 +673,131 @@ camp_status camp_solver_solve_host(camp_solver_t h, int cells,
   return CAMP_OK;
 }
 
+camp_status camp_solver_set_mechanism(camp_solver_t h, int R,
+                                      const int *reactant_a,
+                                      const int *reactant_b,
+                                      const int *product,
+                                      const double *rate_k) {
+  if (!h) return fail(CAMP_EINVAL, "null solver handle");
+  if (R < 0) return fail(CAMP_EINVAL, "R < 0");
+  if (R > 0 && (!reactant_a || !reactant_b || !product || !rate_k))
+    return fail(CAMP_EINVAL, "null mechanism array");
+  const View &v = h->fwd;
+  auto pos = [&](int i, int j) {
+    for (int k = v.rp[i]; k < v.rp[i + 1]; ++k)
+      if (v.ci[k] == j) return k;
+    return -1;
+  };
+  Mechanism M;
+  M.R = R;
+  for (int r = 0; r < R; ++r) {
+    const int a = reactant_a[r], b = reactant_b[r], c = product[r];
+    const double k = rate_k[r];
+    if (a < 0 || a >= v.n || c < 0 || c >= v.n || b >= v.n || b < -1)
+      return fail(CAMP_EINVAL, "species index out of range in reaction %d", r);
+    if (!std::isfinite(k)) return fail(CAMP_EINVAL, "rate constant of reaction %d is not finite", r);
+    // (row, column, concentration factor, sign) of every Jacobian term
+    int t[6][4];
+    int nt = 0;
+    if (b < 0) {
+      int tt[2][4] = {{a, a, -1, -1}, {c, a, -1, 1}};
+      for (int q = 0; q < 2; ++q) for (int z = 0; z < 4; ++z) t[q][z] = tt[q][z];
+      nt = 2;
+    } else {
+      int tt[6][4] = {{a, a, b, -1}, {a, b, a, -1}, {b, a, b, -1},
+                      {b, b, a, -1}, {c, a, b, 1},  {c, b, a, 1}};
+      for (int q = 0; q < 6; ++q) for (int z = 0; z < 4; ++z) t[q][z] = tt[q][z];
+      nt = 6;
+    }
+    for (int q = 0; q < nt; ++q) {
+      const int e = pos(t[q][0], t[q][1]);
+      if (e < 0)
+        return fail(CAMP_EPATTERN, "reaction %d couples (%d, %d), which is not in the pattern",
+                    r, t[q][0], t[q][1]);
+      M.entry.push_back(e);
+      M.spec.push_back(t[q][2]);
+      M.val.push_back(t[q][3] * k);
+    }
+  }
+  for (auto &kv : h->mech.by_lanes) {
+    cudaFree(kv.second.d_cbeg);
+    cudaFree(kv.second.d_cspec);
+    cudaFree(kv.second.d_cval);
+  }
+  h->mech = std::move(M);
+  return CAMP_OK;
+}
+
+camp_status camp_solver_assemble_solve(camp_solver_t h, int cells,
+                                       const double *conc, const double *gamma,
+                                       const double *b, double *x, double tol,
+                                       int maxit, int *iters_out,
+                                       double *resid_out, int *status_out) {
+  if (!h) return fail(CAMP_EINVAL, "null solver handle");
+  if (cells < 0) return fail(CAMP_EINVAL, "cells < 0");
+  if (!(tol > 0.0) || !std::isfinite(tol)) return fail(CAMP_EINVAL, "tol must be finite and > 0");
+  if (maxit < 1) return fail(CAMP_EINVAL, "maxit must be >= 1");
+  if (cells == 0) return CAMP_OK;
+  if (!conc || !gamma || !b || !x || !iters_out || !resid_out)
+    return fail(CAMP_EINVAL, "null array pointer");
+  cudaError_t e = cudaSetDevice(h->device);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
+  View &v = h->fwd;
+  const int Lc = (h->arrangement == CAMP_ARR_WARP) ? h->lanes : auto_lanes(v.n, kAutoRowsPerLane);
+  const int E = Lc ? (v.n + Lc - 1) / Lc : 0;
+  if (Lc == 0 || E > 8)
+    return fail(CAMP_EUNSUPPORTED, "fused assembly supports at most 8 rows per lane (n=%d)", v.n);
+  Schedule *S = nullptr;
+  if ((e = view_schedule(v, Lc, &S)) != cudaSuccess) return cuda_fail(e, "schedule upload");
+  auto it = h->mech.by_lanes.find(Lc);
+  if (it == h->mech.by_lanes.end()) {
+    const int LL = S->L * Lc;
+    std::vector<int> cnt(LL + 1, 0);
+    for (size_t q = 0; q < h->mech.entry.size(); ++q) cnt[S->dst[h->mech.entry[q]] + 1]++;
+    for (int t = 0; t < LL; ++t) cnt[t + 1] += cnt[t];
+    std::vector<int> fillp(cnt.begin(), cnt.end() - 1), cspec(h->mech.entry.size());
+    std::vector<double> cval(h->mech.entry.size());
+    for (size_t q = 0; q < h->mech.entry.size(); ++q) {  // reaction order within a slot
+      const int p = fillp[S->dst[h->mech.entry[q]]]++;
+      cspec[p] = h->mech.spec[q];
+      cval[p] = h->mech.val[q];
+    }
+    MechTerms T;
+    if (cspec.empty()) { cspec.push_back(-1); cval.push_back(0.0); }
+    if ((e = upload(&T.d_cbeg, cnt)) != cudaSuccess ||
+        (e = upload(&T.d_cspec, cspec)) != cudaSuccess ||
+        (e = upload(&T.d_cval, cval)) != cudaSuccess) {
+      cudaFree(T.d_cbeg); cudaFree(T.d_cspec); cudaFree(T.d_cval);
+      return cuda_fail(e, "mechanism upload");
+    }
+    it = h->mech.by_lanes.emplace(Lc, T).first;
+  }
+  int wpb = h->wpb > 0 ? h->wpb : 4;
+  int segA = 0, segV = 0, segStride = 0;
+  size_t smem = warp_smem(v, Lc, S->L, wpb, &segA, &segV, &segStride);
+  while (smem > h->smem_optin && wpb > 1) smem = warp_smem(v, Lc, S->L, --wpb, &segA, &segV, &segStride);
+  if (smem > h->smem_optin) return fail(CAMP_EUNSUPPORTED, "cell does not fit in shared memory");
+  WarpArgs a = {};
+  a.cells = cells; a.n = v.n; a.nnz = v.nnz;
+  a.Lc = Lc; a.log2Lc = ilog2(Lc); a.k = 32 / Lc; a.L = S->L;
+  a.segA = segA; a.segV = segV; a.segStride = segStride;
+  a.ngroups = (cells + a.k - 1) / a.k;
+  a.A = nullptr; a.b = b; a.x = x; a.iters = iters_out; a.resid = resid_out;
+  a.status = status_out; a.sched = S->d_words; a.src = S->d_src;
+  a.dst = S->d_dst; a.padfrom = S->d_padfrom; a.dslot = S->d_dslot;
+  a.tol = tol; a.maxit = maxit; a.x0_given = 0;
+  a.queue = h->d_queue;
+  a.conc = conc; a.gamma = gamma;
+  a.cbeg = it->second.d_cbeg; a.cval = it->second.d_cval; a.cspec = it->second.d_cspec;
+  int occ = 0;
+  if ((e = assemble_occupancy(E, wpb, smem, &occ)) != cudaSuccess) return cuda_fail(e, "occupancy");
+  if (occ < 1) occ = 1;
+  const int grid = std::max(1, std::min((a.ngroups + wpb - 1) / wpb, h->sms * occ));
+  if ((e = launch_assemble(E, a, wpb, grid, smem, h->stream)) != cudaSuccess)
+    return cuda_fail(e, "assembly kernel launch");
+  return CAMP_OK;
+}
+
 camp_status camp_solver_solve_mixed(camp_solver_t h, int cells,
                                     const double *A_vals, const double *b,
                                     double *x, double tol, int max_sweeps,
@@ -680,7 +826,7 @@ camp_status camp_solver_solve_mixed(camp_solver_t h, int cells,
   size_t smem = mixed_smem(v, Lc, S->L, wpb, &segA, &segV);
   while (smem > h->smem_optin && wpb > 1) smem = mixed_smem(v, Lc, S->L, --wpb, &segA, &segV);
   if (smem > h->smem_optin) return fail(CAMP_EUNSUPPORTED, "cell does not fit in shared memory");
-  MixedArgs a;
+  MixedArgs a = {};
   a.cells = cells; a.n = v.n; a.nnz = v.nnz;
   a.Lc = Lc; a.log2Lc = ilog2(Lc); a.k = 32 / Lc; a.L = S->L;
   a.segA = segA; a.segV = segV; a.ngroups = (cells + a.k - 1) / a.k;
@@ -1069,7 +1215,7 @@ camp_status camp_solve_noalloc(int n, int nnz, const int *row_ptr,
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
 
-  WarpArgs a;
+  WarpArgs a = {};
   a.cells = cells; a.n = n; a.nnz = nnz;
   a.Lc = Lc; a.log2Lc = ilog2(Lc); a.k = 32 / Lc; a.L = L;
   a.segA = (L * Lc + 1) & ~1;

@@ -28,10 +28,16 @@ namespace camp {
 #define CAMP_WARP_MINB 2  // with 256 threads per CTA at most: <= 128 registers
 #endif
 
+// Where a group's matrix values come from (template parameter SRC of
+// solve_group): staged from A into shared memory in slot order, read from A
+// through L1 by the SpMV, or assembled in shared memory from the cell's
+// concentrations (A = I - gamma J).
+constexpr int kSrcStaged = 0, kSrcGlobal = 1, kSrcAssembled = 2;
+
 // Solve the k = 32/Lc cells of group g (cells g*k .. g*k+k-1) of one
 // mechanism with this warp.  wbase: the warp's shared-memory region; sch: this
 // lane's column of the SpMV schedule (shared or global memory).
-template <int E, bool ASMEM>
+template <int E, int SRC>
 __device__ __forceinline__ void solve_group(const WarpArgs &a, int g,
                                             double *wbase,
                                             const SchedWord *sch) {
@@ -58,7 +64,25 @@ __device__ __forceinline__ void solve_group(const WarpArgs &a, int g,
   const double *Ac = a.A + (size_t)(has ? c : 0) * nnz;
   const int *srcl = a.src + sl;
   const int LL = a.L * Lc;
-  if (ASMEM) {
+  constexpr bool ASMEM = SRC != kSrcGlobal;
+  if (SRC == kSrcAssembled) {
+    // the cell's concentrations go to the (not yet used) t-product buffer
+    if (has)
+      for (int i = sl; i < n; i += Lc) o2[i] = __ldg(a.conc + (size_t)c * n + i);
+    __syncwarp();
+    const double gam = has ? __ldg(a.gamma + c) : 0.0;
+    for (int t = sl; t < LL; t += Lc) {
+      double acc = 0.0;
+      const int q1 = __ldg(a.cbeg + t + 1);
+      for (int q = __ldg(a.cbeg + t); q < q1; ++q) {
+        const int sp = __ldg(a.cspec + q);
+        acc = fma(__ldg(a.cval + q), sp >= 0 ? o2[sp] : 1.0, acc);
+      }
+      const SchedWord w = sch[(t - sl)];  // this lane's word for slot t
+      const bool dg = __ldg(a.src + t) >= 0 && (w & 0x7ffu) == ((w >> 11) & 0x7ffu);
+      Abase[t] = fma(-gam, acc, dg ? 1.0 : 0.0);
+    }
+  } else if (ASMEM) {
     // coalesced read of the cell's A row, scattered into slot order; each lane
     // zeroes its own padding slots (never a scatter target)
     for (int k = sl; k < nnz; k += Lc) Abase[__ldg(a.dst + k)] = has ? __ldg(Ac + k) : 0.0;
@@ -304,10 +328,9 @@ __device__ __forceinline__ void solve_group(const WarpArgs &a, int g,
 }
 
 // Plain launch: one mechanism, the SpMV schedule in shared memory, groups of
-// k cells assigned to warps in a grid-stride loop.
-template <int E>
-__global__ void __launch_bounds__(256, CAMP_WARP_MINB)
-    warp_bicgstab_kernel(const WarpArgs a) {
+// k cells taken by warps from the dynamic queue (or a grid-stride loop).
+template <int E, int SRC>
+__device__ __forceinline__ void plain_launch_body(const WarpArgs &a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   SchedWord *sch_s = reinterpret_cast<SchedWord *>(smem_raw);
   const int nsch = a.L * a.Lc;
@@ -321,7 +344,7 @@ __global__ void __launch_bounds__(256, CAMP_WARP_MINB)
   const int warps_total = gridDim.x * (blockDim.x >> 5);
   if (!a.queue) {
     for (int g = blockIdx.x * (blockDim.x >> 5) + warp; g < a.ngroups; g += warps_total)
-      solve_group<E, true>(a, g, wbase, sch);
+      solve_group<E, SRC>(a, g, wbase, sch);
     return;
   }
   // dynamic assignment: warps take the next group until none is left
@@ -330,7 +353,7 @@ __global__ void __launch_bounds__(256, CAMP_WARP_MINB)
     if (lane == 0) g = atomicAdd(a.queue, 1u);
     g = __shfl_sync(kFull, g, 0);
     if (g >= (unsigned)a.ngroups) break;
-    solve_group<E, true>(a, (int)g, wbase, sch);
+    solve_group<E, SRC>(a, (int)g, wbase, sch);
   }
   if (lane == 0) {
     // every other warp has taken its last group before counting itself done,
@@ -341,6 +364,19 @@ __global__ void __launch_bounds__(256, CAMP_WARP_MINB)
       atomicExch(a.queue + 1, 0u);
     }
   }
+}
+
+template <int E>
+__global__ void __launch_bounds__(256, CAMP_WARP_MINB)
+    warp_bicgstab_kernel(const WarpArgs a) {
+  plain_launch_body<E, kSrcStaged>(a);
+}
+
+// Fused Jacobian assembly and solve (A = I - gamma J(conc) built per cell).
+template <int E>
+__global__ void __launch_bounds__(256, CAMP_WARP_MINB)
+    assemble_bicgstab_kernel(const WarpArgs a) {
+  plain_launch_body<E, kSrcAssembled>(a);
 }
 
 // Persistent launch over several mechanisms (uneven batching): every warp
@@ -364,7 +400,7 @@ __global__ void __launch_bounds__(256, CAMP_WARP_MINB)
     while (m + 1 < b.nmech && item >= (unsigned)b.item_begin[m + 1]) ++m;
     const WarpArgs &a = b.m[m];
     const SchedWord *sch = a.sched + (lane & (a.Lc - 1));
-    solve_group<E, ASMEM>(a, (int)item - b.item_begin[m], wbase, sch);
+    solve_group<E, ASMEM ? kSrcStaged : kSrcGlobal>(a, (int)item - b.item_begin[m], wbase, sch);
   }
 }
 

@@ -1,0 +1,65 @@
+"""Fused Jacobian assembly and solve against the oracle's plain-C mass-action
+assembly followed by the oracle solve, per cell."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from tests import parity
+
+pytestmark = pytest.mark.gpu
+
+
+def _case(cuda, wid, cells):
+    import torch
+    from paper_2405_17363_gb300 import camp
+    cbs, tol, maxit = synth.workload(wid, cells=cells)
+    cb = cbs[0]
+    m = cb.mech
+    s = camp.Solver(m.row_ptr, m.col_idx)
+    s.set_mechanism(m.reactants[:, 0], m.reactants[:, 1], m.products, m.k)
+    conc = torch.as_tensor(cb.conc, device=cuda)
+    gam = torch.as_tensor(cb.gamma, device=cuda)
+    b = torch.as_tensor(cb.b, device=cuda)
+    x, it, res, st = s.assemble_solve(conc, gam, b, tol, maxit)
+    torch.cuda.synchronize()
+    gpu = dict(x=x.cpu().numpy(), iters=it.cpu().numpy(), resid=res.cpu().numpy(),
+               status=st.cpu().numpy())
+    return camp, s, cb, m, tol, maxit, gpu
+
+
+@pytest.mark.parametrize("wid,cells", [(0, 64), (1, 301), (4, 127)])
+def test_assemble_solve_matches_oracle(cuda, wid, cells):
+    camp, s, cb, m, tol, maxit, gpu = _case(cuda, wid, cells)
+    A = oracle.assemble(m.row_ptr, m.col_idx, m.reactants[:, 0], m.reactants[:, 1],
+                        m.products, m.k, cb.conc, cb.gamma)
+    orc = oracle.solve(m.row_ptr, m.col_idx, A, cb.b, tol, maxit, threads=8)
+    parity.compare(m, A, cb.b, tol, gpu, orc, f"assemble wid{wid}")
+    # the residual of the returned x against the oracle-assembled matrices
+    r = parity.true_resid(m, A, gpu["x"], cb.b)
+    assert np.all(r[gpu["status"] == 0] <= tol * 1.0001)
+    s.close()
+
+
+def test_assemble_solve_full_size_sampled(cuda):
+    camp, s, cb, m, tol, maxit, gpu = _case(cuda, 1, None)
+    assert np.all(gpu["status"] == 0)
+    idx = np.unique(np.r_[0, np.random.default_rng(8).choice(cb.cells, 254, replace=False), cb.cells - 1])
+    A = oracle.assemble(m.row_ptr, m.col_idx, m.reactants[:, 0], m.reactants[:, 1],
+                        m.products, m.k, cb.conc[idx], cb.gamma[idx])
+    orc = oracle.solve(m.row_ptr, m.col_idx, A, cb.b[idx], tol, maxit, threads=8)
+    parity.compare(m, A, cb.b[idx], tol, {k: v[idx] for k, v in gpu.items()}, orc, "assemble full")
+    s.close()
+
+
+def test_mechanism_outside_pattern_is_rejected(cuda):
+    from paper_2405_17363_gb300 import camp
+    m = synth.make_mechanism(8, 6, 3)
+    n = m.n
+    rp = np.arange(n + 1, dtype=np.int32)
+    ci = np.arange(n, dtype=np.int32)   # diagonal pattern only
+    s = camp.Solver(rp, ci)
+    with pytest.raises(camp.CampError) as ex:
+        s.set_mechanism(m.reactants[:, 0], m.reactants[:, 1], m.products, m.k)
+    assert ex.value.code == camp.CAMP_EPATTERN
+    s.close()
