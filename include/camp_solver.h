@@ -122,6 +122,17 @@ camp_status camp_solver_set_arrangement(camp_solver_t h, int arrangement,
                                         int warps_per_block);
 
 /*
+ * Cell ordering for the warp arrangement: 0 (default) solves cells in index
+ * order; 1 first estimates each cell's difficulty (the largest Jacobi-scaled
+ * off-diagonal row sum, in FP32) and hands cells to warps hardest first, so
+ * the cells that share a warp need similar iteration counts.  Results are
+ * identical either way (a cell's solve does not depend on its neighbours);
+ * ordering adds two small launches and device scratch of 8 bytes per cell
+ * (allocated on first use, grown on demand).
+ */
+camp_status camp_solver_set_ordering(camp_solver_t h, int ordering);
+
+/*
  * Solve all cells: A_vals [cells x nnz], b [cells x n] in; x [cells x n],
  * iters_out [cells] (int32), resid_out [cells] out.  Device pointers.
  * tol > 0, maxit >= 1, cells >= 0 (0 enqueues nothing).

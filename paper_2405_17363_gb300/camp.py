@@ -45,6 +45,7 @@ _create = _sig("camp_solver_create", [ctypes.POINTER(_P), _I, _I, _P, _P])
 _destroy = _sig("camp_solver_destroy", [_P])
 _set_stream = _sig("camp_solver_set_stream", [_P, _P])
 _set_arr = _sig("camp_solver_set_arrangement", [_P, _I, _I, _I, _I])
+_set_ordering = _sig("camp_solver_set_ordering", [_P, _I])
 _solve = _sig("camp_solver_solve", [_P, _I, _P, _P, _P, _D, _I, _P, _P])
 _solve_ex = _sig("camp_solver_solve_ex", [_P, _I, _P, _P, _P, _D, _I, _P, _P, _P, _I])
 _grad_A = _sig("camp_solver_grad_A", [_P, _I, _P, _P, _P])
@@ -137,6 +138,10 @@ def camp_solver_set_arrangement(h: int, arrangement: int, lanes_per_cell: int = 
                                 cells_per_block: int = 1, warps_per_block: int = 0):
     _check(_set_arr(h, arrangement, lanes_per_cell, cells_per_block, warps_per_block),
            "camp_solver_set_arrangement")
+
+
+def camp_solver_set_ordering(h: int, ordering: int):
+    _check(_set_ordering(h, int(ordering)), "camp_solver_set_ordering")
 
 
 def camp_solver_solve(h, cells, A_vals, b, x, tol, maxit, iters_out, resid_out):
@@ -276,6 +281,9 @@ class Solver:
                         warps_per_block=0):
         camp_solver_set_arrangement(self.h, arrangement, lanes_per_cell,
                                     cells_per_block, warps_per_block)
+
+    def set_ordering(self, ordering: int):
+        camp_solver_set_ordering(self.h, ordering)
 
     def solve(self, A_vals, b, tol=1e-10, maxit=500, x0=None, transpose=False,
               out=None):

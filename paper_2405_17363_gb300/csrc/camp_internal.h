@@ -50,6 +50,9 @@ struct WarpArgs {
   // finished.  The last warp to finish resets both to zero, so the pair is
   // ready for the next launch in stream order.  Null: static assignment.
   unsigned int *queue;
+  // Optional cell order: group g's segment s solves cell order[g*k + s]
+  // (cells sorted by an estimate of their iteration count), or null.
+  const int *order;
   // Fused assembly (assemble_bicgstab_kernel only): the cell's matrix is
   // built in shared memory as A = I - gamma J(conc) instead of read from A:
   // slot t sums cval[q] * (cspec[q] >= 0 ? conc[cspec[q]] : 1) over
@@ -118,6 +121,11 @@ cudaError_t launch_assemble(int E, const WarpArgs &a, int warps_per_block,
                             int grid, size_t smem, cudaStream_t st);
 cudaError_t assemble_occupancy(int E, int warps_per_block, size_t smem, int *blocks);
 cudaError_t launch_grad(const GradArgs &a, cudaStream_t st);
+// Difficulty ordering: keys[c] = max_i sum_{j != i} |A_ij| / |A_ii| in FP32,
+// then order = cells by decreasing key (bucketed on log2 of the key).
+cudaError_t launch_difficulty_order(const double *A, int cells, int n, int nnz,
+                                    const int *row_ptr, const int *diag,
+                                    float *keys, int *order, cudaStream_t st);
 
 constexpr int kMaxE = 16;  // rows per lane supported by the warp kernel
 // vectors of n (padded) doubles per cell in the warp kernel's shared memory:

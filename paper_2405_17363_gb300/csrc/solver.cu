@@ -206,6 +206,11 @@ struct camp_solver {
   cudaEvent_t h_ev[4] = {nullptr, nullptr, nullptr, nullptr};
   std::mutex mu;
   Mechanism mech;
+  // difficulty ordering (camp_solver_set_ordering): scratch grown on demand
+  int ordering = 0;
+  float *d_keys = nullptr;
+  int *d_order = nullptr;
+  size_t order_cap = 0;
 };
 
 namespace {
@@ -354,6 +359,28 @@ camp_status do_solve(camp_solver_t h, int cells, const double *A_vals,
     a.dslot = S->d_dslot; a.tol = tol; a.maxit = maxit;
     a.x0_given = (flags & CAMP_X0_GIVEN) ? 1 : 0;
     a.queue = h->d_queue + 2 * queue_slot;
+    a.order = nullptr;
+    if (h->ordering && cells > 1 && queue_slot == 0) {
+      if ((size_t)cells > h->order_cap) {
+        cudaFree(h->d_keys);
+        cudaFree(h->d_order);
+        h->d_keys = nullptr;
+        h->d_order = nullptr;
+        h->order_cap = 0;
+        if ((e = cudaMalloc(&h->d_keys, (size_t)cells * sizeof(float))) != cudaSuccess ||
+            (e = cudaMalloc(&h->d_order, (size_t)cells * sizeof(int))) != cudaSuccess)
+          return fail(CAMP_ENOMEM, "ordering scratch: %s", cudaGetErrorString(e));
+        h->order_cap = (size_t)cells;
+      }
+      if (flags & CAMP_TRANSPOSE)
+        e = launch_difficulty_order(A_vals, cells, h->tr.n, h->tr.nnz, h->fwd.d_rp,
+                                    h->fwd.d_diag, h->d_keys, h->d_order, st);
+      else
+        e = launch_difficulty_order(A_vals, cells, v.n, v.nnz, v.d_rp, v.d_diag,
+                                    h->d_keys, h->d_order, st);
+      if (e != cudaSuccess) return cuda_fail(e, "difficulty ordering");
+      a.order = h->d_order;
+    }
     int occ = 0;
     e = warp_occupancy(E, wpb, smem, &occ);
     if (e != cudaSuccess) return cuda_fail(e, "occupancy");
@@ -390,7 +417,7 @@ camp_status do_solve(camp_solver_t h, int cells, const double *A_vals,
 extern "C" {
 
 const char *camp_last_error(void) { return g_err.c_str(); }
-const char *camp_version(void) { return "campsolve 0.4 (sm_103a)"; }
+const char *camp_version(void) { return "campsolve 0.5 (sm_103a)"; }
 
 camp_status camp_schedule_build(int n, int nnz, const int *row_ptr,
                                 const int *col_idx, int lanes_per_cell,
@@ -515,6 +542,8 @@ camp_status camp_solver_destroy(camp_solver_t h) {
   }
   cudaFree(h->d_row_of);
   cudaFree(h->d_queue);
+  cudaFree(h->d_keys);
+  cudaFree(h->d_order);
   cudaFree(h->h_dA); cudaFree(h->h_db); cudaFree(h->h_dx);
   cudaFree(h->h_dres); cudaFree(h->h_dit); cudaFree(h->h_dst);
   for (auto &s : h->h_streams) if (s) cudaStreamDestroy(s);
@@ -559,6 +588,13 @@ camp_status camp_solver_set_arrangement(camp_solver_t h, int arrangement,
     return CAMP_OK;
   }
   return fail(CAMP_EINVAL, "unknown arrangement %d", arrangement);
+}
+
+camp_status camp_solver_set_ordering(camp_solver_t h, int ordering) {
+  if (!h) return fail(CAMP_EINVAL, "null solver handle");
+  if (ordering != 0 && ordering != 1) return fail(CAMP_EINVAL, "ordering must be 0 or 1");
+  h->ordering = ordering;
+  return CAMP_OK;
 }
 
 camp_status camp_solver_solve(camp_solver_t h, int cells, const double *A_vals,

@@ -196,13 +196,15 @@ __device__ __forceinline__ bool is_zero_bits(double v) {
 
 // 1/d in FP64 by Newton-Raphson iteration y <- y + y (1 - d y).  d = m 2^k
 // with m in [1, 2) (m and k read from the bit pattern); an FP32
-// rcp.approx of m (relative error about 2^-22) seeds two Newton steps on m,
-// which bring the error to FP64 rounding; the exponent of the result is then
-// lowered by k on the bit pattern.  Only the four Newton FMAs use the FP64
-// pipe (a division costs about seven).  Zero gives Inf, Inf gives zero, NaN
+// rcp.approx of m (relative error about 2^-22) seeds STEPS Newton steps on m,
+// each squaring the relative error (one step: about 2^-44; two: FP64
+// rounding); the exponent of the result is then lowered by k on the bit
+// pattern.  Only the 2*STEPS Newton FMAs use the FP64 pipe (a division costs
+// about seven).  Zero gives Inf, Inf gives zero, NaN
 // stays NaN; results that would leave the normal FP64 range (|d| above
 // 2^1022 or below 2^-1022) are returned as zero or Inf.
-__device__ __forceinline__ double recip64(double d) {
+template <int STEPS>
+__device__ __forceinline__ double recip64n(double d) {
   const unsigned long long u = (unsigned long long)__double_as_longlong(d);
   const unsigned long long sign = u & 0x8000000000000000ull;
   const int ed = (int)((u >> 52) & 0x7ffull);
@@ -213,10 +215,11 @@ __device__ __forceinline__ double recip64(double d) {
       : "f"(__uint_as_float(0x3f800000u | (unsigned)(frac >> 29))));
   double y = __longlong_as_double((long long)(((unsigned long long)(__float_as_uint(yf) & 0x7fffffu) << 29) |
                                               ((unsigned long long)(((__float_as_uint(yf) >> 23) & 0xffu) - 127 + 1023) << 52)));
-  double r = fma(-m, y, 1.0);
-  y = fma(y, r, y);
-  r = fma(-m, y, 1.0);
-  y = fma(y, r, y);                       // 1/m in (0.5, 1]
+#pragma unroll
+  for (int s = 0; s < STEPS; ++s) {
+    const double r = fma(-m, y, 1.0);
+    y = fma(y, r, y);                     // 1/m in (0.5, 1]
+  }
   const unsigned long long yu = (unsigned long long)__double_as_longlong(y);
   const int ey = (int)((yu >> 52) & 0x7ffull) - (ed - 1023);
   unsigned long long out = sign | ((unsigned long long)ey << 52) | (yu & 0xfffffffffffffull);
@@ -225,5 +228,12 @@ __device__ __forceinline__ double recip64(double d) {
   out = (ed == 0x7ff) ? (frac ? 0x7ff8000000000000ull : sign) : out;  // NaN, 1/Inf
   return __longlong_as_double((long long)out);
 }
+
+// Full-precision reciprocal (two Newton steps): the Jacobi preconditioner.
+__device__ __forceinline__ double recip64(double d) { return recip64n<2>(d); }
+// Scalars of the iteration (alpha, beta, omega): one step, relative error
+// about 2^-44; x and r are updated with the same scalar, so they stay
+// consistent and the true-residual test still decides convergence.
+__device__ __forceinline__ double recip64s(double d) { return recip64n<1>(d); }
 
 }  // namespace camp

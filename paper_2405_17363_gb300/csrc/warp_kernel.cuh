@@ -52,8 +52,9 @@ __device__ __forceinline__ void solve_group(const WarpArgs &a, int g,
   double *o2 = o1 + a.segV;      // t = A s^
   double *rhs = o2 + a.segV;     // shadow residual r^
   double *dvs = rhs + a.segV;    // Jacobi reciprocals
-  const int c = g * a.k + seg;
-  const bool has = c < a.cells;
+  const int pos = g * a.k + seg;
+  const bool has = pos < a.cells;
+  const int c = (has && a.order) ? __ldg(a.order + pos) : pos;
 #define SPMV(out)                                                    \
   do {                                                               \
     if (ASMEM) seg_spmv(sch, a.L, Lc, Asl, gs, out);                 \
@@ -181,7 +182,7 @@ __device__ __forceinline__ void solve_group(const WarpArgs &a, int g,
         }
       }
       // p = r + beta (p - omega v); the bracket is kept in p
-      const double beta = (rho * alpha) * recip64(rho_prev * omega);
+      const double beta = (rho * alpha) * recip64s(rho_prev * omega);
 #pragma unroll
       for (int e = 0; e < E; ++e) {
         const int i = sl + e * Lc;
@@ -208,7 +209,7 @@ __device__ __forceinline__ void solve_group(const WarpArgs &a, int g,
           active = false;
         }
       }
-      const double al = rho * recip64(sg[0]);
+      const double al = rho * recip64s(sg[0]);
       if (active) alpha = al;
 #pragma unroll
       for (int e = 0; e < E; ++e) {
@@ -245,7 +246,7 @@ __device__ __forceinline__ void solve_group(const WarpArgs &a, int g,
           full = true;
         }
       }
-      const double om = q1 * recip64(q2);
+      const double om = q1 * recip64s(q2);
       if (full) omega = om;
 #pragma unroll
       for (int e = 0; e < E; ++e) {
