@@ -1,0 +1,36 @@
+// Self-test entry point: runs the warp kernels' numerical building blocks
+// (reciprocals, FP64<->FP32 conversions on the integer pipe, segment sums) on
+// caller data so tests can compare them with exact host references.
+#include "warp_common.cuh"
+
+namespace camp {
+namespace {
+
+__global__ void selftest_kernel(int op, int n, const double *in, double *out, int lanes) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const bool ok = i < n;
+  const double v = ok ? in[i] : 0.0;
+  double r = 0.0;
+  if (op == 0) r = recip64(v);
+  else if (op == 1) r = recip64s(v);
+  else if (op == 2) r = f2d_exact(d2f_rn(v));
+  else if (op == 3) r = seg_sum_exact(v, lanes);     // whole warp takes part
+  else if (op == 4) {
+    double a[1] = {v};
+    seg_sum<1>(a, lanes);
+    r = a[0];
+  }
+  if (ok) out[i] = r;
+}
+
+}  // namespace
+}  // namespace camp
+
+extern "C" camp_status camp_selftest(int op, int n, const double *in, double *out,
+                                     int lanes, void *stream) {
+  if (op < 0 || op > 4 || n < 0 || !in || !out) return CAMP_EINVAL;
+  if (op >= 3 && (lanes < 1 || lanes > 32 || (lanes & (lanes - 1)) || n % 32)) return CAMP_EINVAL;
+  if (n == 0) return CAMP_OK;
+  camp::selftest_kernel<<<(n + 255) / 256, 256, 0, (cudaStream_t)stream>>>(op, n, in, out, lanes);
+  return cudaGetLastError() == cudaSuccess ? CAMP_OK : CAMP_ECUDA;
+}

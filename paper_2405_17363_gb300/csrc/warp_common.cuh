@@ -236,4 +236,41 @@ __device__ __forceinline__ double recip64(double d) { return recip64n<2>(d); }
 // consistent and the true-residual test still decides convergence.
 __device__ __forceinline__ double recip64s(double d) { return recip64n<1>(d); }
 
+// Sum of v over the Lc lanes of each segment on the integer pipe.  Every
+// term m 2^(e-1075) (53-bit integer m) is aligned to the segment's largest
+// exponent as a signed 64-bit fixed-point number with 5 guard bits (room for
+// 32 terms), the integers are summed exactly with xor shuffles, and the total
+// is rounded once to FP64 (nearest, ties to even).  The error is at most one
+// rounding plus 2^-57 of the largest term per term, every lane gets the same
+// bits, and no FP64 instruction is issued.  Any NaN or Inf gives NaN; totals
+// below the normal FP64 range flush to zero.
+__device__ __forceinline__ double seg_sum_exact(double v, int Lc) {
+  const unsigned long long u = (unsigned long long)__double_as_longlong(v);
+  const int e = (int)((u >> 52) & 0x7ffull);
+  const unsigned long long frac = u & 0xfffffffffffffull;
+  const unsigned long long m = e ? (frac | (1ull << 52)) : frac;
+  const int ee = e ? e : 1;
+  int emax = ee;
+  for (int off = Lc >> 1; off > 0; off >>= 1) emax = max(emax, __shfl_xor_sync(kFull, emax, off));
+  const int sh = emax - ee;
+  long long f = sh >= 58 ? 0ll : (long long)((m << 5) >> sh);
+  f = (u >> 63) ? -f : f;
+  for (int off = Lc >> 1; off > 0; off >>= 1) f += __shfl_xor_sync(kFull, f, off);
+  const unsigned long long neg = f < 0 ? 1ull : 0ull;
+  const unsigned long long a = (unsigned long long)(f < 0 ? -f : f);
+  const int lz = __clzll((long long)a);
+  const unsigned long long an = a << (lz & 63);
+  unsigned long long mant = an >> 11;
+  const unsigned rem = (unsigned)(an & 0x7ffull);
+  mant += (rem > 0x400u || (rem == 0x400u && (mant & 1ull))) ? 1ull : 0ull;
+  int E = (63 - lz) + emax - 57;
+  E += (mant >> 53) ? 1 : 0;                 // rounding carried into a new bit
+  mant = (mant >> 53) ? (mant >> 1) : mant;
+  unsigned long long out = (neg << 63) | ((unsigned long long)E << 52) | (mant & 0xfffffffffffffull);
+  out = (E <= 0 || a == 0ull) ? (neg << 63) : out;            // zero / flush
+  out = (E >= 0x7ff) ? ((neg << 63) | (0x7ffull << 52)) : out;  // overflow
+  out = (emax == 0x7ff) ? 0x7ff8000000000000ull : out;         // NaN or Inf present
+  return __longlong_as_double((long long)out);
+}
+
 }  // namespace camp

@@ -24,6 +24,34 @@
 
 namespace camp {
 
+#ifndef CAMP_EXACT_SUMS
+#define CAMP_EXACT_SUMS 1  // segment sums on the integer pipe (0: FP64 shuffle tree)
+#endif
+
+__device__ __forceinline__ double ssum1(double v, int Lc) {
+  if (CAMP_EXACT_SUMS) return seg_sum_exact(v, Lc);
+  double a[1] = {v};
+  seg_sum<1>(a, Lc);
+  return a[0];
+}
+__device__ __forceinline__ void ssum2(double &a, double &b, int Lc) {
+  if (CAMP_EXACT_SUMS) {
+    a = seg_sum_exact(a, Lc);
+    b = seg_sum_exact(b, Lc);
+  } else {
+    seg_sum2(a, b, Lc);
+  }
+}
+__device__ __forceinline__ void ssum3(double &a, double &b, double &c, int Lc) {
+  if (CAMP_EXACT_SUMS) {
+    a = seg_sum_exact(a, Lc);
+    b = seg_sum_exact(b, Lc);
+    c = seg_sum_exact(c, Lc);
+  } else {
+    seg_sum3(a, b, c, Lc);
+  }
+}
+
 #ifndef CAMP_WARP_MINB
 #define CAMP_WARP_MINB 2  // with 256 threads per CTA at most: <= 128 registers
 #endif
@@ -115,8 +143,7 @@ __device__ __forceinline__ void solve_group(const WarpArgs &a, int g,
       s[e] = 0.0;
       acc[0] = fma(bi, bi, acc[0]);
     }
-    seg_sum<1>(acc, Lc);
-    bb = acc[0];
+    bb = ssum1(acc[0], Lc);
   }
   const double thr = (tol * tol) * bb;  // (tol ||b||)^2
   int st = -1, it = 0, nbreak = 0;
@@ -152,7 +179,7 @@ __device__ __forceinline__ void solve_group(const WarpArgs &a, int g,
       double acc[1] = {0.0};
 #pragma unroll
       for (int e = 0; e < E; ++e) acc[0] = fma(r[e], r[e], acc[0]);
-      seg_sum<1>(acc, Lc);
+      acc[0] = ssum1(acc[0], Lc);
       if (restart) {
 #pragma unroll
         for (int e = 0; e < E; ++e) {
@@ -199,7 +226,7 @@ __device__ __forceinline__ void solve_group(const WarpArgs &a, int g,
         const int i = sl + e * Lc;
         sg[0] = fma(rhs[i], o1[i], sg[0]);
       }
-      seg_sum<1>(sg, Lc);
+      sg[0] = ssum1(sg[0], Lc);
       if (active) {
         if (!is_finite_bits(sg[0])) {
           nonfin = true;
@@ -231,7 +258,7 @@ __device__ __forceinline__ void solve_group(const WarpArgs &a, int g,
         q1 = fma(t, s[e], q1);
         q2 = fma(t, t, q2);
       }
-      seg_sum3(q0, q1, q2, Lc);
+      ssum3(q0, q1, q2, Lc);
       bool full = false;
       if (active) {
         if (le_nonneg(q0, thr)) {
@@ -263,7 +290,7 @@ __device__ __forceinline__ void solve_group(const WarpArgs &a, int g,
         hr = fma(rhs[sl + e * Lc], r[e], hr);
         rr = fma(r[e], r[e], rr);
       }
-      seg_sum2(hr, rr, Lc);
+      ssum2(hr, rr, Lc);
       if (full) {
         nbreak = 0;
         if (le_nonneg(rr, thr)) {
@@ -291,7 +318,7 @@ __device__ __forceinline__ void solve_group(const WarpArgs &a, int g,
       s[e] = bi - o1[i];  // s holds the true residual here
       rt2[0] = fma(s[e], s[e], rt2[0]);
     }
-    seg_sum<1>(rt2, Lc);
+    rt2[0] = ssum1(rt2[0], Lc);
     if (fin) {
       fin = false;
       resid = sqrt(rt2[0] * recip64(bb));
