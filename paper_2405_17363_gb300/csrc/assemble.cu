@@ -5,8 +5,7 @@ namespace camp {
 
 template <int E>
 static cudaError_t launch_e(const WarpArgs &a, int wpb, int grid, size_t smem, cudaStream_t st) {
-  cudaError_t e = cudaFuncSetAttribute(assemble_bicgstab_kernel<E>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = ensure_max_smem((const void *)assemble_bicgstab_kernel<E>);
   if (e != cudaSuccess) return e;
   assemble_bicgstab_kernel<E><<<grid, wpb * 32, smem, st>>>(a);
   return cudaGetLastError();
@@ -14,8 +13,7 @@ static cudaError_t launch_e(const WarpArgs &a, int wpb, int grid, size_t smem, c
 
 template <int E>
 static cudaError_t occ_e(int wpb, size_t smem, int *blocks) {
-  cudaError_t e = cudaFuncSetAttribute(assemble_bicgstab_kernel<E>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = ensure_max_smem((const void *)assemble_bicgstab_kernel<E>);
   if (e != cudaSuccess) return e;
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, assemble_bicgstab_kernel<E>,
                                                        wpb * 32, smem);

@@ -6,9 +6,7 @@ namespace camp {
 
 template <int E, bool S>
 static cudaError_t prep(int wpb, size_t smem, int *blocks) {
-  cudaError_t e = cudaFuncSetAttribute(batch_bicgstab_kernel<E, S>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)smem);
+  cudaError_t e = ensure_max_smem((const void *)batch_bicgstab_kernel<E, S>);
   if (e != cudaSuccess) return e;
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(
       blocks, batch_bicgstab_kernel<E, S>, wpb * 32, smem);

@@ -319,9 +319,8 @@ __global__ void __launch_bounds__(1024) block_bicgstab_kernel(const BlockArgs a)
 }
 
 cudaError_t block_set_smem(size_t smem) {
-  return cudaFuncSetAttribute(block_bicgstab_kernel,
-                              cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)smem);
+  (void)smem;
+  return ensure_max_smem((const void *)block_bicgstab_kernel);
 }
 
 cudaError_t launch_block(const BlockArgs &a, int threads, size_t smem,

@@ -54,14 +54,15 @@ struct WarpArgs {
   // (cells sorted by an estimate of their iteration count), or null.
   const int *order;
   // Fused assembly (assemble_bicgstab_kernel only): the cell's matrix is
-  // built in shared memory as A = I - gamma J(conc) instead of read from A:
-  // slot t sums cval[q] * (cspec[q] >= 0 ? conc[cspec[q]] : 1) over
-  // q in [cbeg[t], cbeg[t+1]) (its mass-action terms in reaction order).
+  // built in shared memory as A = I - gamma J(conc) instead of read from A.
+  // Lane sl runs tcount terms p: J[slot (tmeta >> 11) * Lc + sl] +=
+  // tval * (conc[(tmeta & 0x7ff) - 1] or 1 when that field is 0); arrays
+  // are laid out [p][lane], padding terms add zero.
   const double *conc;      // [cells x n]
   const double *gamma;     // [cells]
-  const int *cbeg;         // [L*Lc + 1]
-  const double *cval;      // [terms] sign * rate constant
-  const int *cspec;        // [terms] species whose concentration multiplies, or -1
+  const double *tval;      // [tcount x Lc] sign * rate constant
+  const int *tmeta;        // [tcount x Lc] species + 1 | slot row << 11
+  int tcount;
 };
 
 // Persistent launch over up to kMaxMech mechanisms: mechanism m owns work
@@ -128,6 +129,11 @@ cudaError_t launch_difficulty_order(const double *A, int cells, int n, int nnz,
                                     float *keys, int *order, cudaStream_t st);
 
 constexpr int kMaxE = 16;  // rows per lane supported by the warp kernel
+
+// Raise a kernel's dynamic shared-memory limit to the device maximum once per
+// (kernel, device): setting the attribute on every launch serialises
+// otherwise-concurrent work on some drivers.
+cudaError_t ensure_max_smem(const void *kernel);
 // vectors of n (padded) doubles per cell in the warp kernel's shared memory:
 // gathered vector, two products, shadow residual, Jacobi reciprocals
 constexpr int kWarpVectors = 5;

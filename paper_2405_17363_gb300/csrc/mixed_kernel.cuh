@@ -76,8 +76,7 @@ __global__ void __launch_bounds__(256, 2) mixed_refine_kernel(const MixedArgs a)
         xv[e] = 0.0;
         acc[0] = fma(bi, bi, acc[0]);
       }
-      seg_sum<1>(acc, Lc);
-      bb = acc[0];
+      bb = seg_sum_exact(acc[0], Lc);
     }
     const double thr = (a.tol * a.tol) * bb;  // (tol ||b||)^2
     int st = -1, sweeps = 0, inner = 0;
@@ -109,7 +108,7 @@ __global__ void __launch_bounds__(256, 2) mixed_refine_kernel(const MixedArgs a)
         r[e] = pass > 0 ? bi - o64[i] : bi;
         rr[0] = fma(r[e], r[e], rr[0]);
       }
-      seg_sum<1>(rr, Lc);
+      rr[0] = seg_sum_exact(rr[0], Lc);
       if (!done) {
         // ||r|| <= tol ||b|| on the bit patterns; the relative residual itself
         // (a square root and a division) is formed once, at the end

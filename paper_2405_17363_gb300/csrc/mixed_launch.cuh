@@ -3,17 +3,13 @@
 #define CAMP_MIXED_DEFINE(E)                                                    \
   cudaError_t launch_mixed_##E(const MixedArgs &a, int wpb, int grid,           \
                                size_t smem, cudaStream_t st) {                  \
-    cudaError_t e = cudaFuncSetAttribute(                                       \
-        mixed_refine_kernel<E>, cudaFuncAttributeMaxDynamicSharedMemorySize,    \
-        (int)smem);                                                             \
+    cudaError_t e = ensure_max_smem((const void *)mixed_refine_kernel<E>);      \
     if (e != cudaSuccess) return e;                                             \
     mixed_refine_kernel<E><<<grid, wpb * 32, smem, st>>>(a);                    \
     return cudaGetLastError();                                                  \
   }                                                                             \
   cudaError_t occ_mixed_##E(int wpb, size_t smem, int *blocks) {                \
-    cudaError_t e = cudaFuncSetAttribute(                                       \
-        mixed_refine_kernel<E>, cudaFuncAttributeMaxDynamicSharedMemorySize,    \
-        (int)smem);                                                             \
+    cudaError_t e = ensure_max_smem((const void *)mixed_refine_kernel<E>);      \
     if (e != cudaSuccess) return e;                                             \
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(                       \
         blocks, mixed_refine_kernel<E>, wpb * 32, smem);                        \

@@ -72,6 +72,35 @@ cudaError_t mixed_occupancy(int E, int wpb, size_t smem, int *blocks) {
   }
 }
 
+constexpr int kHostChunks = 8;        // pipeline depth of camp_solver_solve_host
+constexpr int kHostSolveStreams = 4;  // concurrent chunk solves
+
+cudaError_t ensure_max_smem(const void *kernel) {
+  // fixed-size record (no heap allocation: the allocation-free entry point
+  // launches through here too)
+  static std::mutex mu;
+  static const void *done_kernel[512];
+  static int done_dev[512];
+  static int ndone = 0;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lock(mu);
+  for (int i = 0; i < ndone; ++i)
+    if (done_kernel[i] == kernel && done_dev[i] == dev) return cudaSuccess;
+  int optin = 0;
+  if ((e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev)) != cudaSuccess)
+    return e;
+  if ((e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, optin)) != cudaSuccess)
+    return e;
+  if (ndone < 512) {
+    done_kernel[ndone] = kernel;
+    done_dev[ndone] = dev;
+    ++ndone;
+  }
+  return cudaSuccess;
+}
+
 namespace {
 
 thread_local std::string g_err;
@@ -172,8 +201,9 @@ cudaError_t upload(T **dst, const std::vector<T> &src) {
 // signed rate constant) and, per lanes-per-cell choice, the terms grouped by
 // schedule slot on the device.
 struct MechTerms {
-  int *d_cbeg = nullptr, *d_cspec = nullptr;
-  double *d_cval = nullptr;
+  int count = 0;               // terms per lane (padded)
+  int *d_tmeta = nullptr;
+  double *d_tval = nullptr;
 };
 struct Mechanism {
   int R = 0;
@@ -195,15 +225,18 @@ struct camp_solver {
   View fwd, tr;
   int *d_row_of = nullptr;  // forward view: row of entry k
   // dynamic group queues of the warp kernel, one pair per stream the handle
-  // uses: [0..1] its own stream, [2..5] the two streams of solve_host
+  // uses: pair 0 its own stream, pairs 1.. the solve streams of solve_host
   unsigned int *d_queue = nullptr;
   int arrangement = CAMP_ARR_AUTO, lanes = 0, cpb = 1, wpb = 0;
   // staging for camp_solver_solve_host
   double *h_dA = nullptr, *h_db = nullptr, *h_dx = nullptr, *h_dres = nullptr;
   int *h_dit = nullptr, *h_dst = nullptr;
   size_t h_cap_cells = 0;
-  cudaStream_t h_streams[2] = {nullptr, nullptr};
-  cudaEvent_t h_ev[4] = {nullptr, nullptr, nullptr, nullptr};
+  // solve_host pipeline: [0] host-to-device copies, [1] device-to-host
+  // copies, [2 ..] solves (round robin, so the solves of consecutive chunks
+  // overlap); per chunk an event after its input copy and one after its solve
+  cudaStream_t h_streams[2 + kHostSolveStreams] = {};
+  cudaEvent_t h_in[kHostChunks] = {}, h_done[kHostChunks] = {};
   std::mutex mu;
   Mechanism mech;
   // difficulty ordering (camp_solver_set_ordering): scratch grown on demand
@@ -417,7 +450,7 @@ camp_status do_solve(camp_solver_t h, int cells, const double *A_vals,
 extern "C" {
 
 const char *camp_last_error(void) { return g_err.c_str(); }
-const char *camp_version(void) { return "campsolve 0.6 (sm_103a)"; }
+const char *camp_version(void) { return "campsolve 0.7 (sm_103a)"; }
 
 camp_status camp_schedule_build(int n, int nnz, const int *row_ptr,
                                 const int *col_idx, int lanes_per_cell,
@@ -517,7 +550,7 @@ camp_status camp_solver_create(camp_solver_t *out, int n, int nnz,
       (e = upload(&t.d_diag, t.diag)) != cudaSuccess ||
       (e = upload(&t.d_perm, t.perm)) != cudaSuccess ||
       (e = upload(&h->d_row_of, row_of)) != cudaSuccess ||
-      (e = upload(&h->d_queue, std::vector<unsigned int>(6, 0u))) != cudaSuccess) {
+      (e = upload(&h->d_queue, std::vector<unsigned int>(2 * (1 + kHostSolveStreams), 0u))) != cudaSuccess) {
     free_view(h->fwd);
     free_view(h->tr);
     cudaFree(h->d_row_of);
@@ -536,9 +569,8 @@ camp_status camp_solver_destroy(camp_solver_t h) {
   free_view(h->fwd);
   free_view(h->tr);
   for (auto &kv : h->mech.by_lanes) {
-    cudaFree(kv.second.d_cbeg);
-    cudaFree(kv.second.d_cspec);
-    cudaFree(kv.second.d_cval);
+    cudaFree(kv.second.d_tmeta);
+    cudaFree(kv.second.d_tval);
   }
   cudaFree(h->d_row_of);
   cudaFree(h->d_queue);
@@ -547,7 +579,8 @@ camp_status camp_solver_destroy(camp_solver_t h) {
   cudaFree(h->h_dA); cudaFree(h->h_db); cudaFree(h->h_dx);
   cudaFree(h->h_dres); cudaFree(h->h_dit); cudaFree(h->h_dst);
   for (auto &s : h->h_streams) if (s) cudaStreamDestroy(s);
-  for (auto &ev : h->h_ev) if (ev) cudaEventDestroy(ev);
+  for (auto &ev : h->h_in) if (ev) cudaEventDestroy(ev);
+  for (auto &ev : h->h_done) if (ev) cudaEventDestroy(ev);
   delete h;
   return CAMP_OK;
 }
@@ -662,50 +695,69 @@ camp_status camp_solver_solve_host(camp_solver_t h, int cells,
       return fail(CAMP_ENOMEM, "staging allocation: %s", cudaGetErrorString(e));
     h->h_cap_cells = (size_t)cells;
   }
-  for (int q = 0; q < 2; ++q)
+  for (int q = 0; q < 2 + kHostSolveStreams; ++q)
     if (!h->h_streams[q] &&
         (e = cudaStreamCreateWithFlags(&h->h_streams[q], cudaStreamNonBlocking)) != cudaSuccess)
       return cuda_fail(e, "stream create");
+  for (int q = 0; q < kHostChunks; ++q)
+    if ((!h->h_in[q] && (e = cudaEventCreateWithFlags(&h->h_in[q], cudaEventDisableTiming)) != cudaSuccess) ||
+        (!h->h_done[q] && (e = cudaEventCreateWithFlags(&h->h_done[q], cudaEventDisableTiming)) != cudaSuccess))
+      return cuda_fail(e, "event create");
+  cudaStream_t sin = h->h_streams[0], sout = h->h_streams[1];
   // order after earlier work on the handle's stream
   cudaEvent_t ev0;
   if ((e = cudaEventCreateWithFlags(&ev0, cudaEventDisableTiming)) != cudaSuccess)
     return cuda_fail(e, "event create");
   cudaEventRecord(ev0, h->stream);
-  cudaStreamWaitEvent(h->h_streams[0], ev0, 0);
-  cudaStreamWaitEvent(h->h_streams[1], ev0, 0);
+  for (int q = 0; q < 2 + kHostSolveStreams; ++q) cudaStreamWaitEvent(h->h_streams[q], ev0, 0);
   cudaEventDestroy(ev0);
-  // chunked pipeline: copy chunk q+1 in while chunk q solves, alternating streams
-  const int nchunk = cells >= 4096 ? 4 : 1;
+  // pipeline: every chunk's input is copied back to back on the copy-in
+  // stream (the host link stays busy), its solve starts on the next solve
+  // stream once that copy has landed (solves of consecutive chunks overlap, so
+  // a chunk's tail does not idle the GPU), its results go back on the
+  // copy-out stream once the solve is done
+  const int nchunk = cells >= kHostChunks * 512 ? kHostChunks : 1;
   const int per = (cells + nchunk - 1) / nchunk;
   camp_status rs = CAMP_OK;
   for (int q = 0; q < nchunk; ++q) {
     const int c0 = q * per;
     const int cn = std::min(per, cells - c0);
     if (cn <= 0) break;
-    cudaStream_t s = h->h_streams[q & 1];
     cudaMemcpyAsync(h->h_dA + (size_t)c0 * nnz, A_vals + (size_t)c0 * nnz,
-                    (size_t)cn * nnz * 8, cudaMemcpyHostToDevice, s);
+                    (size_t)cn * nnz * 8, cudaMemcpyHostToDevice, sin);
     cudaMemcpyAsync(h->h_db + (size_t)c0 * n, b + (size_t)c0 * n,
-                    (size_t)cn * n * 8, cudaMemcpyHostToDevice, s);
+                    (size_t)cn * n * 8, cudaMemcpyHostToDevice, sin);
+    cudaEventRecord(h->h_in[q], sin);
+  }
+  for (int q = 0; q < nchunk; ++q) {
+    const int c0 = q * per;
+    const int cn = std::min(per, cells - c0);
+    if (cn <= 0) break;
+    cudaStream_t scomp = h->h_streams[2 + q % kHostSolveStreams];
+    cudaStreamWaitEvent(scomp, h->h_in[q], 0);
     rs = do_solve(h, cn, h->h_dA + (size_t)c0 * nnz, h->h_db + (size_t)c0 * n,
                   h->h_dx + (size_t)c0 * n, tol, maxit, h->h_dit + c0,
-                  h->h_dres + c0, h->h_dst + c0, 0, s, 1 + (q & 1));
+                  h->h_dres + c0, h->h_dst + c0, 0, scomp, 1 + q % kHostSolveStreams);
     if (rs != CAMP_OK) break;
+    cudaEventRecord(h->h_done[q], scomp);
+    cudaStreamWaitEvent(sout, h->h_done[q], 0);
     cudaMemcpyAsync(x + (size_t)c0 * n, h->h_dx + (size_t)c0 * n,
-                    (size_t)cn * n * 8, cudaMemcpyDeviceToHost, s);
+                    (size_t)cn * n * 8, cudaMemcpyDeviceToHost, sout);
     cudaMemcpyAsync(iters_out + c0, h->h_dit + c0, (size_t)cn * 4,
-                    cudaMemcpyDeviceToHost, s);
+                    cudaMemcpyDeviceToHost, sout);
     cudaMemcpyAsync(resid_out + c0, h->h_dres + c0, (size_t)cn * 8,
-                    cudaMemcpyDeviceToHost, s);
+                    cudaMemcpyDeviceToHost, sout);
     if (status_out)
       cudaMemcpyAsync(status_out + c0, h->h_dst + c0, (size_t)cn * 4,
-                      cudaMemcpyDeviceToHost, s);
+                      cudaMemcpyDeviceToHost, sout);
   }
-  cudaError_t e0 = cudaStreamSynchronize(h->h_streams[0]);
-  cudaError_t e1 = cudaStreamSynchronize(h->h_streams[1]);
+  cudaError_t es = cudaSuccess;
+  for (int q = 0; q < 2 + kHostSolveStreams; ++q) {
+    const cudaError_t eq = cudaStreamSynchronize(h->h_streams[q]);
+    if (es == cudaSuccess) es = eq;
+  }
   if (rs != CAMP_OK) return rs;
-  if (e0 != cudaSuccess) return cuda_fail(e0, "solve_host");
-  if (e1 != cudaSuccess) return cuda_fail(e1, "solve_host");
+  if (es != cudaSuccess) return cuda_fail(es, "solve_host");
   return CAMP_OK;
 }
 
@@ -756,9 +808,8 @@ camp_status camp_solver_set_mechanism(camp_solver_t h, int R,
     }
   }
   for (auto &kv : h->mech.by_lanes) {
-    cudaFree(kv.second.d_cbeg);
-    cudaFree(kv.second.d_cspec);
-    cudaFree(kv.second.d_cval);
+    cudaFree(kv.second.d_tmeta);
+    cudaFree(kv.second.d_tval);
   }
   h->mech = std::move(M);
   return CAMP_OK;
@@ -785,25 +836,31 @@ camp_status camp_solver_assemble_solve(camp_solver_t h, int cells,
     return fail(CAMP_EUNSUPPORTED, "fused assembly supports at most 8 rows per lane (n=%d)", v.n);
   Schedule *S = nullptr;
   if ((e = view_schedule(v, Lc, &S)) != cudaSuccess) return cuda_fail(e, "schedule upload");
+  if (S->L > 2047) return fail(CAMP_EUNSUPPORTED, "more than 2047 slots per lane");
   auto it = h->mech.by_lanes.find(Lc);
   if (it == h->mech.by_lanes.end()) {
-    const int LL = S->L * Lc;
-    std::vector<int> cnt(LL + 1, 0);
-    for (size_t q = 0; q < h->mech.entry.size(); ++q) cnt[S->dst[h->mech.entry[q]] + 1]++;
-    for (int t = 0; t < LL; ++t) cnt[t + 1] += cnt[t];
-    std::vector<int> fillp(cnt.begin(), cnt.end() - 1), cspec(h->mech.entry.size());
-    std::vector<double> cval(h->mech.entry.size());
-    for (size_t q = 0; q < h->mech.entry.size(); ++q) {  // reaction order within a slot
-      const int p = fillp[S->dst[h->mech.entry[q]]]++;
-      cspec[p] = h->mech.spec[q];
-      cval[p] = h->mech.val[q];
+    // every lane's terms (its slots' Jacobian terms, reaction order), padded
+    // to the longest lane and laid out [term][lane]
+    std::vector<std::vector<std::pair<double, int>>> lane(Lc);
+    for (size_t q = 0; q < h->mech.entry.size(); ++q) {
+      const int t = S->dst[h->mech.entry[q]];
+      lane[t % Lc].push_back({h->mech.val[q], (h->mech.spec[q] + 1) | ((t / Lc) << 11)});
     }
+    size_t M = 1;
+    for (auto &l : lane) M = std::max(M, l.size());
+    std::vector<double> tval(M * Lc, 0.0);
+    std::vector<int> tmeta(M * Lc, 0);
+    for (int q = 0; q < Lc; ++q)
+      for (size_t p = 0; p < lane[q].size(); ++p) {
+        tval[p * Lc + q] = lane[q][p].first;
+        tmeta[p * Lc + q] = lane[q][p].second;
+      }
     MechTerms T;
-    if (cspec.empty()) { cspec.push_back(-1); cval.push_back(0.0); }
-    if ((e = upload(&T.d_cbeg, cnt)) != cudaSuccess ||
-        (e = upload(&T.d_cspec, cspec)) != cudaSuccess ||
-        (e = upload(&T.d_cval, cval)) != cudaSuccess) {
-      cudaFree(T.d_cbeg); cudaFree(T.d_cspec); cudaFree(T.d_cval);
+    T.count = (int)M;
+    if ((e = upload(&T.d_tval, tval)) != cudaSuccess ||
+        (e = upload(&T.d_tmeta, tmeta)) != cudaSuccess) {
+      cudaFree(T.d_tval);
+      cudaFree(T.d_tmeta);
       return cuda_fail(e, "mechanism upload");
     }
     it = h->mech.by_lanes.emplace(Lc, T).first;
@@ -824,7 +881,7 @@ camp_status camp_solver_assemble_solve(camp_solver_t h, int cells,
   a.tol = tol; a.maxit = maxit; a.x0_given = 0;
   a.queue = h->d_queue;
   a.conc = conc; a.gamma = gamma;
-  a.cbeg = it->second.d_cbeg; a.cval = it->second.d_cval; a.cspec = it->second.d_cspec;
+  a.tval = it->second.d_tval; a.tmeta = it->second.d_tmeta; a.tcount = it->second.count;
   int occ = 0;
   if ((e = assemble_occupancy(E, wpb, smem, &occ)) != cudaSuccess) return cuda_fail(e, "occupancy");
   if (occ < 1) occ = 1;

@@ -95,21 +95,25 @@ __device__ __forceinline__ void solve_group(const WarpArgs &a, int g,
   const int LL = a.L * Lc;
   constexpr bool ASMEM = SRC != kSrcGlobal;
   if (SRC == kSrcAssembled) {
+    // J accumulates in place in the lane's own slots, then A = I - gamma J
+    for (int t = sl; t < LL; t += Lc) Abase[t] = 0.0;
     // the cell's concentrations go to the (not yet used) t-product buffer
     if (has)
       for (int i = sl; i < n; i += Lc) o2[i] = __ldg(a.conc + (size_t)c * n + i);
     __syncwarp();
     const double gam = has ? __ldg(a.gamma + c) : 0.0;
+    const double *tv = a.tval + sl;
+    const int *tm = a.tmeta + sl;
+    for (int p = 0; p < a.tcount; ++p) {
+      const int meta = __ldg(tm + p * Lc);
+      const int sp = (meta & 0x7ff) - 1;
+      double *dst = Abase + ((meta >> 11) & 0x7ff) * Lc + sl;
+      *dst = fma(__ldg(tv + p * Lc), sp >= 0 ? o2[sp] : 1.0, *dst);
+    }
     for (int t = sl; t < LL; t += Lc) {
-      double acc = 0.0;
-      const int q1 = __ldg(a.cbeg + t + 1);
-      for (int q = __ldg(a.cbeg + t); q < q1; ++q) {
-        const int sp = __ldg(a.cspec + q);
-        acc = fma(__ldg(a.cval + q), sp >= 0 ? o2[sp] : 1.0, acc);
-      }
-      const SchedWord w = sch[(t - sl)];  // this lane's word for slot t
+      const SchedWord w = sch[t - sl];  // this lane's word for slot t
       const bool dg = __ldg(a.src + t) >= 0 && (w & 0x7ffu) == ((w >> 11) & 0x7ffu);
-      Abase[t] = fma(-gam, acc, dg ? 1.0 : 0.0);
+      Abase[t] = fma(-gam, Abase[t], dg ? 1.0 : 0.0);
     }
   } else if (ASMEM) {
     // coalesced read of the cell's A row, scattered into slot order; each lane
