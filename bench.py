@@ -303,6 +303,73 @@ def run_uneven_case(args):
     print(json.dumps({"case": "uneven", **res}), flush=True)
 
 
+def lockstep_waste(iters, k):
+    """Lane-iterations idle because the k cells sharing a warp run until the
+    slowest converges, as a fraction of the useful ones (cells in index order)."""
+    it = np.asarray(iters, dtype=np.float64)
+    pad = (-len(it)) % k
+    grp = np.concatenate([it, np.zeros(pad)]).reshape(-1, k)
+    return float((grp.max(axis=1, keepdims=True) - grp).sum() / max(it.sum(), 1.0))
+
+
+def run_variability_case(args):
+    """--case variability: 'realistic' cells (per-cell concentrations and
+    gamma, as generated) against 'ideal' cells (every cell a copy of the first
+    one), as in the paper's two initial-condition set-ups (Sec. 4.2): the
+    spread of iteration counts, the lockstep waste it causes in the
+    warp-packed solve, and the throughput of the plain and persistent launches."""
+    import torch
+    from paper_2405_17363_gb300 import camp
+    dev = torch.device("cuda", 0)
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+    rows = []
+    for wid in (WORKLOAD_ID, 2):
+        cbs, tol, maxit = synth.workload(wid)
+        for setup in ("realistic", "ideal"):
+            solvers, As, bs, cells = [], [], [], 0
+            for cb in cbs:
+                A, b = cb.A_vals, cb.b
+                if setup == "ideal":
+                    A = np.repeat(A[:1], cb.cells, axis=0)
+                    b = np.repeat(b[:1], cb.cells, axis=0)
+                solvers.append(camp.Solver(cb.mech.row_ptr, cb.mech.col_idx))
+                As.append(torch.as_tensor(np.ascontiguousarray(A), device=dev))
+                bs.append(torch.as_tensor(np.ascontiguousarray(b), device=dev))
+                cells += cb.cells
+            outs = [sv.solve(a, v, tol, maxit) for sv, a, v in zip(solvers, As, bs)]
+
+            def plain():
+                for sv, a, v, o in zip(solvers, As, bs, outs):
+                    sv.solve(a, v, tol, maxit, out=o)
+            tp = sum(time_steps(plain, flush, stream, args.steps, 3)) / args.steps
+            batch = camp.Batch(solvers)
+            bo = batch.solve(As, bs, tol, maxit)
+            tb = sum(time_steps(lambda: batch.solve(As, bs, tol, maxit, out=bo), flush, stream,
+                                args.steps, 3)) / args.steps
+            it = np.concatenate([o[1].cpu().numpy() for o in outs])
+            waste = [lockstep_waste(o[1].cpu().numpy(), 32 // sv_lanes(sv.n))
+                     for sv, o in zip(solvers, outs)]
+            rows.append({"workload": synth.WORKLOADS[wid][0], "setup": setup, "cells": cells,
+                         "iters_mean": float(it.mean()), "iters_std": float(it.std()),
+                         "iters_p99": float(np.percentile(it, 99)), "iters_max": int(it.max()),
+                         "lockstep_waste_by_mechanism": waste,
+                         "plain_ms": tp, "plain_value": cells / (tp * 1e-3),
+                         "persistent_ms": tb, "persistent_value": cells / (tb * 1e-3)})
+            batch.close()
+            for sv in solvers:
+                sv.close()
+    print(json.dumps({"case": "variability", "unit": UNIT, "rows": rows}), flush=True)
+
+
+def sv_lanes(n):
+    """Lanes per cell of the automatic warp arrangement (at most five rows per lane)."""
+    lc = 1
+    while (n + lc - 1) // lc > 5 and lc < 32:
+        lc *= 2
+    return lc
+
+
 def run_arrangements_case(args):
     """--case arrangements: the paper's kernel-configuration study (Sec. 3.2,
     Sec. 5.2) on the headline workload: every arrangement's solve time and
@@ -352,7 +419,8 @@ def main():
                     help="auto | warp:<lanes per cell>[:<warps per block>] | block:<cells per block>")
     ap.add_argument("--mode", default="fp64", choices=["fp64", "mixed"],
                     help="fp64: plain FP64 solve (the headline); mixed: FP32-inner refinement")
-    ap.add_argument("--case", default="headline", choices=["headline", "uneven", "arrangements"],
+    ap.add_argument("--case", default="headline",
+                    choices=["headline", "uneven", "arrangements", "variability"],
                     help="headline: the 80-species 10k-cell FP64 solve; uneven: time the "
                          "persistent multi-mechanism batch as the step (for profiling)")
     ap.add_argument("--skip-extras", action="store_true",
@@ -371,6 +439,8 @@ def main():
         return run_uneven_case(args)
     if args.case == "arrangements":
         return run_arrangements_case(args)
+    if args.case == "variability":
+        return run_variability_case(args)
 
     import torch
     import torch.distributed as dist

@@ -63,3 +63,12 @@ def test_reference_arm_runs_on_rank_zero_only():
                        text=True, timeout=300)
     assert r.returncode == 0
     assert r.stdout.strip() == ""
+
+
+def test_lockstep_waste_definition():
+    sys.path.insert(0, ROOT)
+    import bench
+    # pairs (3, 5) and (4, 4): the first pair idles 2 lane-iterations of 16 useful
+    assert bench.lockstep_waste([3, 5, 4, 4], 2) == pytest.approx(2 / 16)
+    assert bench.lockstep_waste([7] * 6, 2) == 0.0
+    assert bench.lockstep_waste([2, 6, 1], 2) == pytest.approx((4 + 1) / 9)
