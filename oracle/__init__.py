@@ -60,6 +60,10 @@ def _load():
             lib.orc_transpose_pattern.argtypes = [I, P, P, P, P, P]
             lib.orc_assemble_cell.restype = I
             lib.orc_assemble_cell.argtypes = [I, P, P, I, P, P, P, P, P, D, P]
+            lib.orc_rates_cell.restype = None
+            lib.orc_rates_cell.argtypes = [I, I, P, P, P, P, P, P]
+            lib.orc_newton_cell.restype = I
+            lib.orc_newton_cell.argtypes = [I, P, P, I, P, P, P, P, P, D, P, D, I, D, I, P, P, P]
             lib.orc_grad_A_cell.restype = None
             lib.orc_grad_A_cell.argtypes = [I, P, P, P, P, P]
             _lib = lib
@@ -156,6 +160,49 @@ def assemble(row_ptr, col_idx, reactant_a, reactant_b, product, k, conc, gamma):
         if code != 0:
             raise ValueError("a Jacobian entry lies outside the pattern")
     return A
+
+
+def rates(reactant_a, reactant_b, product, k, y):
+    """f(y) [cells, n] of the mass-action mechanism."""
+    lib = _load()
+    ra, rb, pr = _i32(reactant_a), _i32(reactant_b), _i32(product)
+    kk = _f64(k)
+    Y = _f64(np.atleast_2d(y))
+    F = np.zeros_like(Y)
+    for c in range(Y.shape[0]):
+        lib.orc_rates_cell(Y.shape[1], int(ra.shape[0]), _p(ra), _p(rb), _p(pr), _p(kk),
+                           _p(np.ascontiguousarray(Y[c])), _p(F[c]))
+    return F
+
+
+def newton(row_ptr, col_idx, reactant_a, reactant_b, product, k, a_hist, gamma, y0,
+           newton_tol=1e-10, max_newton=20, lin_tol=1e-10, lin_maxit=500):
+    """Newton corrector of G(y) = y - gamma f(y) - a = 0 per cell (see
+    camp_oracle.c).  Returns dict(y, newton_iters, lin_iters, upd, status)."""
+    lib = _load()
+    rp, ci = _i32(row_ptr), _i32(col_idx)
+    ra, rb, pr = _i32(reactant_a), _i32(reactant_b), _i32(product)
+    kk = _f64(k)
+    Ah = _f64(np.atleast_2d(a_hist))
+    g = _f64(np.atleast_1d(gamma))
+    Y = np.array(np.atleast_2d(y0), dtype=np.float64, copy=True)
+    cells = Y.shape[0]
+    out = dict(y=Y, newton_iters=np.zeros(cells, np.int32), lin_iters=np.zeros(cells, np.int32),
+               upd=np.zeros(cells), status=np.zeros(cells, np.int32))
+    ni, li, up = ctypes.c_int(), ctypes.c_int(), ctypes.c_double()
+    for c in range(cells):
+        yc = np.ascontiguousarray(Y[c])
+        st = lib.orc_newton_cell(Y.shape[1], _p(rp), _p(ci), int(ra.shape[0]), _p(ra), _p(rb),
+                                 _p(pr), _p(kk), _p(np.ascontiguousarray(Ah[c])), float(g[c]),
+                                 _p(yc), float(newton_tol), int(max_newton), float(lin_tol),
+                                 int(lin_maxit), ctypes.byref(ni), ctypes.byref(li),
+                                 ctypes.byref(up))
+        Y[c] = yc
+        out["newton_iters"][c] = ni.value
+        out["lin_iters"][c] = li.value
+        out["upd"][c] = up.value
+        out["status"][c] = st
+    return out
 
 
 def adjoint(row_ptr, col_idx, A_vals, x, w, tol=1e-10, maxit=500, threads=1):

@@ -466,3 +466,68 @@ int orc_assemble_cell(int n, const int *rp, const int *ci, int R,
       A[q] = ((ci[q] == i) ? 1.0 : 0.0) - gamma * A[q];
   return 0;
 }
+
+/* ---- Newton corrector of the implicit step around the solve ------------ */
+
+/* f_i(y) = dy_i/dt: every reaction r has rate k[r] y_a (first order) or
+ * k[r] y_a y_b (second order); it is subtracted from its reactants' rows and
+ * added to its product's row (Sec. 2.2: f_i sums the reactions' terms). */
+void orc_rates_cell(int n, int R, const int *ra, const int *rb, const int *pr,
+                    const double *k, const double *y, double *f) {
+  for (int i = 0; i < n; ++i) f[i] = 0.0;
+  for (int r = 0; r < R; ++r) {
+    const int a = ra[r], b = rb[r], c = pr[r];
+    const double rate = (b < 0) ? k[r] * y[a] : k[r] * y[a] * y[b];
+    f[a] = f[a] - rate;
+    if (b >= 0) f[b] = f[b] - rate;
+    f[c] = f[c] + rate;
+  }
+}
+
+/*
+ * The nonlinear system of one implicit (BDF) step, G(y) = y - gamma f(y) - a
+ * = 0 (a: the step's history term, e.g. y^n for backward Euler), by Newton's
+ * method from the initial guess in y: each iteration assembles the Newton
+ * matrix A = I - gamma J(y), solves A d = -G(y) with the BiCGSTAB above
+ * (lin_tol, lin_maxit) and sets y += d; converged when ||d||_2 <= newton_tol
+ * ||y||_2.  The paper's CVODE/BDF step needs exactly these linear systems
+ * (Sec. 2.2); the solver loop around them is its future work (Sec. 6).
+ * Returns 0 converged, 1 iterations exhausted, 2 linear solve failed,
+ * 3 non-finite.  newton_iters = iterations run, lin_iters = BiCGSTAB
+ * iterations summed, upd = final ||d|| / ||y||.
+ */
+int orc_newton_cell(int n, const int *rp, const int *ci, int R, const int *ra,
+                    const int *rb, const int *pr, const double *k,
+                    const double *a_hist, double gamma, double *y,
+                    double newton_tol, int max_newton, double lin_tol,
+                    int lin_maxit, int *newton_iters, int *lin_iters,
+                    double *upd) {
+  const int nnz = rp[n];
+  double *A = (double *)malloc(sizeof(double) * (size_t)(nnz > 0 ? nnz : 1));
+  double *w = (double *)malloc(sizeof(double) * 3 * (size_t)(n > 0 ? n : 1));
+  double *f = w, *rhs = w + n, *d = w + 2 * n;
+  int status = 1, it = 0, lin = 0;
+  double u = 0.0;
+  for (it = 0; it < max_newton;) {
+    orc_rates_cell(n, R, ra, rb, pr, k, y, f);
+    for (int i = 0; i < n; ++i) rhs[i] = -(y[i] - gamma * f[i] - a_hist[i]);
+    if (orc_assemble_cell(n, rp, ci, R, ra, rb, pr, k, y, gamma, A) != 0) { status = 2; break; }
+    int li = 0;
+    double res = 0.0;
+    const int ls = orc_bicgstab_cell(n, rp, ci, A, rhs, lin_tol, lin_maxit, 0, d, &li, &res);
+    lin += li;
+    ++it;
+    if (ls != ORC_CONVERGED) { status = (ls == ORC_NONFINITE) ? 3 : 2; break; }
+    for (int i = 0; i < n; ++i) y[i] += d[i];
+    const double dn = sqrt(dot(n, d, d)), yn = sqrt(dot(n, y, y));
+    u = (yn > 0.0) ? dn / yn : dn;
+    if (!isfinite(u)) { status = 3; break; }
+    if (u <= newton_tol) { status = 0; break; }
+  }
+  *newton_iters = it;
+  *lin_iters = lin;
+  *upd = u;
+  free(A);
+  free(w);
+  return status;
+}

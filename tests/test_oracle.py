@@ -430,3 +430,53 @@ def test_assembly_rejects_entries_outside_the_pattern():
     with pytest.raises(ValueError):
         oracle.assemble(rp, ci, m.reactants[:, 0], m.reactants[:, 1], m.products, m.k,
                         np.ones((1, m.n)), [0.1])
+
+
+def test_rates_match_independent_numpy_rates():
+    cbs, _, _ = synth.workload(1, cells=5)
+    cb = cbs[0]
+    m = cb.mech
+    F = oracle.rates(m.reactants[:, 0], m.reactants[:, 1], m.products, m.k, cb.conc)
+    np.testing.assert_allclose(F, m.rates(cb.conc), rtol=1e-13, atol=1e-30)
+
+
+def test_newton_linear_mechanism_is_one_step():
+    """First-order reactions only: f is linear, G(y) = (I - gamma J) y - a, so
+    Newton lands on the dense solution in one step and confirms it with a
+    negligible second update."""
+    m = synth.make_mechanism(12, 16, 3)
+    keep = m.reactants[:, 1] < 0
+    ra, rb, pr, k = m.reactants[keep, 0], m.reactants[keep, 1], m.products[keep], m.k[keep]
+    rng = np.random.default_rng(0)
+    a = rng.uniform(0.1, 1.0, (4, m.n))
+    gam = np.array([1e-3, 1e-2, 0.1, 1.0])
+    out = oracle.newton(m.row_ptr, m.col_idx, ra, rb, pr, k, a, gam, a.copy(),
+                        newton_tol=1e-9, lin_tol=1e-13)
+    assert np.all(out["status"] == 0) and np.all(out["newton_iters"] == 2)
+    for c in range(4):
+        J = np.zeros((m.n, m.n))
+        for r in range(len(k)):
+            J[ra[r], ra[r]] -= k[r]
+            J[pr[r], ra[r]] += k[r]
+        y = np.linalg.solve(np.eye(m.n) - gam[c] * J, a[c])
+        np.testing.assert_allclose(out["y"][c], y, rtol=1e-11)
+
+
+def test_newton_root_satisfies_the_step_equation():
+    """The full (second-order) mechanism: the converged y makes the implicit
+    step's residual y - gamma f(y) - a vanish, with f evaluated by the
+    generator's independent rate code, and agrees with SciPy's root finder."""
+    optimize = pytest.importorskip("scipy.optimize")
+    cbs, _, _ = synth.workload(1, cells=6)
+    cb = cbs[0]
+    m = cb.mech
+    a = cb.conc
+    out = oracle.newton(m.row_ptr, m.col_idx, m.reactants[:, 0], m.reactants[:, 1],
+                        m.products, m.k, a, cb.gamma, a.copy(), newton_tol=1e-12)
+    assert np.all(out["status"] == 0)
+    for c in range(6):
+        y = out["y"][c]
+        G = y - cb.gamma[c] * m.rates(y) - a[c]
+        assert np.linalg.norm(G) <= 1e-10 * np.linalg.norm(a[c])
+        sol = optimize.root(lambda z: z - cb.gamma[c] * m.rates(z) - a[c], a[c], tol=1e-15)
+        np.testing.assert_allclose(y, sol.x, rtol=1e-8, atol=1e-12 * np.abs(a[c]).max())
