@@ -293,6 +293,41 @@ def time_fused(camp, cb, tol, maxit, flush, stream, dev, steps=200):
             "hbm_bytes_per_cell": 8 * m.n + 8 + 16 * m.n + 12, "converged": conv}
 
 
+def time_newton(camp, cb, flush, stream, dev, steps=50, newton_tol=1e-10, lin_tol=1e-10,
+                lin_maxit=500):
+    """The device Newton corrector of the implicit step on the same cells:
+    history term a = the cells' concentrations, initial guess y = a; every
+    step copies the guess in and runs all Newton iterations of all cells in
+    one launch.  The unit is Newton solves (cells) per second."""
+    import torch
+    m = cb.mech
+    s = camp.Solver(m.row_ptr, m.col_idx)
+    s.set_mechanism(m.reactants[:, 0], m.reactants[:, 1], m.products, m.k)
+    a = torch.as_tensor(cb.conc, device=dev)
+    gam = torch.as_tensor(cb.gamma, device=dev)
+    out = s.newton_solve(a, gam, a, newton_tol, 20, lin_tol, lin_maxit)
+    y = out["y"]
+
+    def step():
+        y.copy_(a)
+        camp.camp_solver_newton_solve(s.h, cb.cells, a, gam, y, newton_tol, 20, lin_tol,
+                                      lin_maxit, out["newton_iters"], out["lin_iters"],
+                                      out["upd"], out["resid"], out["status"])
+    t = time_steps(step, flush, stream, steps, 5)
+    ms = sum(t) / steps
+    ni = out["newton_iters"].double()
+    res = {"value": cb.cells / (ms * 1e-3), "unit": "cell Newton solves/s", "ms_per_step": ms,
+           "what": "Newton corrector of y - gamma f(y) - a = 0 per cell on the device "
+                   "(rates, assembly, BiCGSTAB per iteration), newton_tol 1e-10",
+           "newton_iters_mean": float(ni.mean().item()),
+           "newton_iters_max": int(ni.max().item()),
+           "lin_iters_per_newton": float((out["lin_iters"].double() / ni.clamp(min=1))
+                                         .mean().item()),
+           "converged": int((out["status"] == 0).sum().item())}
+    s.close()
+    return res
+
+
 def run_uneven_case(args):
     """--case uneven: the persistent batch alone, timed as the step."""
     import torch
@@ -499,6 +534,7 @@ def main():
     e2e = None
     uneven = None
     fused = None
+    newton = None
     if not args.skip_extras:
         if args.mode == "fp64":
             mt = time_steps(solve_mixed, flush, stream, 200, 5)
@@ -513,6 +549,7 @@ def main():
                 "speedup_vs_fp64": ms_step / mms}
         e2e = time_e2e(camp, solver, cb, C, tol, maxit, args.e2e_steps, world, dev)
         fused = time_fused(camp, cb, tol, maxit, flush, stream, dev)
+        newton = time_newton(camp, cb, flush, stream, dev)
         uneven = time_uneven(camp, dev, flush, stream) if rank == 0 else None
 
     if rank == 0:
@@ -552,6 +589,8 @@ def main():
             line["uneven_batch"] = uneven
         if fused is not None:
             line["fused_assembly"] = fused
+        if newton is not None:
+            line["newton_step"] = newton
         if cpu is not None:
             line["cpu_baseline"] = cpu
         print(json.dumps(line), flush=True)

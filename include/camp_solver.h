@@ -316,6 +316,38 @@ camp_status camp_solver_assemble_solve(camp_solver_t h, int cells,
                                        int maxit, int *iters_out,
                                        double *resid_out, int *status_out);
 
+/*
+ * Device Newton corrector of one implicit (BDF) step per cell.  The systems
+ * the paper solves are the Newton systems of CVODE's BDF step (Sec. 2.2,
+ * A = I - gamma J); moving the loop around them onto the GPU is its future
+ * work (Sec. 6).  For every cell c this solves G(y) = y - gamma[c] f(y) -
+ * a_hist[c] = 0, f the mass-action rates of the mechanism set by
+ * camp_solver_set_mechanism, by Newton's method from the initial guess in y:
+ * each iteration evaluates f(y), assembles A = I - gamma[c] J(y) in shared
+ * memory, solves A d = -G(y) with the Jacobi-BiCGSTAB of camp_solver_solve_ex
+ * (lin_tol, lin_maxit, zero initial guess) and sets y += d; it stops when
+ * ||d||_2 <= newton_tol ||y||_2 (||d||_2 <= newton_tol when y = 0), after
+ * max_newton iterations, or when a linear solve does not converge.  One
+ * kernel launch runs every iteration of every cell.
+ *
+ * a_hist, y [cells x n] row-major, gamma [cells]; y is read as the initial
+ * guess and replaced by the last iterate.  newton_iters_out (iterations run),
+ * lin_iters_out (BiCGSTAB iterations summed), upd_out (last ||d|| / ||y||),
+ * resid_out (relative residual of the last linear solve) [cells] are
+ * required; status_out [cells] may be NULL: 0 converged, 1 iterations
+ * exhausted, 2 linear solve failed (y keeps the iterate before it),
+ * 3 non-finite.  All device pointers, written on the handle's stream.
+ * CAMP_EINVAL for a non-positive or non-finite tolerance, max_newton < 0 or
+ * lin_maxit < 1; CAMP_EUNSUPPORTED beyond 8 rows per lane (n <= 256).
+ */
+camp_status camp_solver_newton_solve(camp_solver_t h, int cells,
+                                     const double *a_hist, const double *gamma,
+                                     double *y, double newton_tol, int max_newton,
+                                     double lin_tol, int lin_maxit,
+                                     int *newton_iters_out, int *lin_iters_out,
+                                     double *upd_out, double *resid_out,
+                                     int *status_out);
+
 /* Thread-local message describing the last error (never NULL). */
 const char *camp_last_error(void);
 

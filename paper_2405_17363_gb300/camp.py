@@ -54,6 +54,8 @@ _solve_mixed = _sig("camp_solver_solve_mixed",
                     [_P, _I, _P, _P, _P, _D, _I, _D, _I, _P, _P, _P, _P])
 _set_mech = _sig("camp_solver_set_mechanism", [_P, _I, _P, _P, _P, _P])
 _assemble_solve = _sig("camp_solver_assemble_solve", [_P, _I, _P, _P, _P, _P, _D, _I, _P, _P, _P])
+_newton_solve = _sig("camp_solver_newton_solve",
+                     [_P, _I, _P, _P, _P, _D, _I, _D, _I, _P, _P, _P, _P, _P])
 _batch_create = _sig("camp_batch_create", [ctypes.POINTER(_P), _I, _P])
 _batch_destroy = _sig("camp_batch_destroy", [_P])
 _batch_set_stream = _sig("camp_batch_set_stream", [_P, _P])
@@ -220,6 +222,21 @@ def camp_solver_assemble_solve(h, cells, conc, gamma, b, x, tol, maxit, iters_ou
            "camp_solver_assemble_solve")
 
 
+def camp_solver_newton_solve(h, cells, a_hist, gamma, y, newton_tol, max_newton, lin_tol,
+                             lin_maxit, newton_iters_out, lin_iters_out, upd_out, resid_out,
+                             status_out=None):
+    camp_solver_set_stream(h)
+    _check(_newton_solve(h, int(cells), _dptr(a_hist, torch.float64, "a_hist"),
+                         _dptr(gamma, torch.float64, "gamma"), _dptr(y, torch.float64, "y"),
+                         float(newton_tol), int(max_newton), float(lin_tol), int(lin_maxit),
+                         _dptr(newton_iters_out, torch.int32, "newton_iters_out"),
+                         _dptr(lin_iters_out, torch.int32, "lin_iters_out"),
+                         _dptr(upd_out, torch.float64, "upd_out"),
+                         _dptr(resid_out, torch.float64, "resid_out"),
+                         _dptr(status_out, torch.int32, "status_out")),
+           "camp_solver_newton_solve")
+
+
 def camp_batch_create(solver_handles) -> int:
     arr = (_P * len(solver_handles))(*solver_handles)
     h = _P()
@@ -320,6 +337,24 @@ class Solver:
                    torch.empty(cells, dtype=torch.int32, device=dev))
         camp_solver_assemble_solve(self.h, cells, conc, gamma, b, out[0], tol, maxit,
                                    out[1], out[2], out[3])
+        return out
+
+    def newton_solve(self, a_hist, gamma, y0, newton_tol=1e-10, max_newton=20, lin_tol=1e-10,
+                     lin_maxit=500):
+        """Newton corrector of y - gamma_c f(y) - a_c = 0 per cell from y0 (one
+        launch); returns dict(y, newton_iters, lin_iters, upd, resid, status)."""
+        cells = a_hist.shape[0]
+        dev = a_hist.device
+        y = y0.clone()
+        out = dict(y=y,
+                   newton_iters=torch.empty(cells, dtype=torch.int32, device=dev),
+                   lin_iters=torch.empty(cells, dtype=torch.int32, device=dev),
+                   upd=torch.empty(cells, dtype=torch.float64, device=dev),
+                   resid=torch.empty(cells, dtype=torch.float64, device=dev),
+                   status=torch.empty(cells, dtype=torch.int32, device=dev))
+        camp_solver_newton_solve(self.h, cells, a_hist, gamma, y, newton_tol, max_newton,
+                                 lin_tol, lin_maxit, out["newton_iters"], out["lin_iters"],
+                                 out["upd"], out["resid"], out["status"])
         return out
 
     def grad_A(self, lam, x, out=None):

@@ -63,6 +63,18 @@ struct WarpArgs {
   const double *tval;      // [tcount x Lc] sign * rate constant
   const int *tmeta;        // [tcount x Lc] species + 1 | slot row << 11
   int tcount;
+  // Newton corrector (newton_bicgstab_kernel only): lane sl accumulates
+  // f[row sl + e*Lc] += rval * y[a] * (y[b] or 1) over its rcount terms,
+  // rmeta = (a + 1) | (b + 1) << 11 | e << 22 ([p][lane]); the history term
+  // is read from b, y (in: initial guess, out: solution) from x, the linear
+  // tolerance and iteration cap from tol and maxit.
+  const double *rval;
+  const int *rmeta;
+  int rcount;
+  double newton_tol;
+  int max_newton;
+  int *newton_iters;       // [cells]
+  double *upd;             // [cells] final ||d|| / ||y||
 };
 
 // Persistent launch over up to kMaxMech mechanisms: mechanism m owns work
@@ -121,6 +133,10 @@ cudaError_t block_set_smem(size_t smem);
 cudaError_t launch_assemble(int E, const WarpArgs &a, int warps_per_block,
                             int grid, size_t smem, cudaStream_t st);
 cudaError_t assemble_occupancy(int E, int warps_per_block, size_t smem, int *blocks);
+// device Newton corrector around the fused assembly + solve, E in 1..8
+cudaError_t launch_newton(int E, const WarpArgs &a, int warps_per_block,
+                          int grid, size_t smem, cudaStream_t st);
+cudaError_t newton_occupancy(int E, int warps_per_block, size_t smem, int *blocks);
 cudaError_t launch_grad(const GradArgs &a, cudaStream_t st);
 // Difficulty ordering: keys[c] = max_i sum_{j != i} |A_ij| / |A_ii| in FP32,
 // then order = cells by decreasing key (bucketed on log2 of the key).

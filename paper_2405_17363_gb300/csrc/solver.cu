@@ -201,14 +201,25 @@ cudaError_t upload(T **dst, const std::vector<T> &src) {
 // signed rate constant) and, per lanes-per-cell choice, the terms grouped by
 // schedule slot on the device.
 struct MechTerms {
-  int count = 0;               // terms per lane (padded)
+  int count = 0;               // Jacobian terms per lane (padded)
   int *d_tmeta = nullptr;
   double *d_tval = nullptr;
+  int rcount = 0;              // rate terms per lane (padded)
+  int *d_rmeta = nullptr;
+  double *d_rval = nullptr;
+  void release() {
+    cudaFree(d_tmeta);
+    cudaFree(d_tval);
+    cudaFree(d_rmeta);
+    cudaFree(d_rval);
+  }
 };
 struct Mechanism {
   int R = 0;
-  std::vector<int> entry, spec;
+  std::vector<int> entry, spec;  // Jacobian terms: CSR entry, factor species
   std::vector<double> val;
+  std::vector<int> rrow, ra, rb;  // rate terms: row of f, factor species
+  std::vector<double> rk;         // signed rate constant
   std::map<int, MechTerms> by_lanes;
 };
 
@@ -305,12 +316,12 @@ int bank_spread_stride(int need, int k) {
 
 // Warp kernel shared-memory bytes for one CTA.
 size_t warp_smem(const View &v, int Lc, int L, int wpb, int *segA, int *segV,
-                 int *segStride) {
+                 int *segStride, int vectors = kWarpVectors) {
   const int k = 32 / Lc;
   const int E = (v.n + Lc - 1) / Lc;
   *segA = (L * Lc + 1) & ~1;  // A in slot order
   *segV = ((E * Lc + 1) + 1) & ~1;
-  *segStride = bank_spread_stride(*segA + kWarpVectors * *segV, k);
+  *segStride = bank_spread_stride(*segA + vectors * *segV, k);
   const size_t sch = sched_smem_bytes(L * Lc);
   return sch + (size_t)wpb * k * (size_t)*segStride * 8;
 }
@@ -568,10 +579,7 @@ camp_status camp_solver_destroy(camp_solver_t h) {
   cudaStreamSynchronize(h->stream);
   free_view(h->fwd);
   free_view(h->tr);
-  for (auto &kv : h->mech.by_lanes) {
-    cudaFree(kv.second.d_tmeta);
-    cudaFree(kv.second.d_tval);
-  }
+  for (auto &kv : h->mech.by_lanes) kv.second.release();
   cudaFree(h->d_row_of);
   cudaFree(h->d_queue);
   cudaFree(h->d_keys);
@@ -806,12 +814,115 @@ camp_status camp_solver_set_mechanism(camp_solver_t h, int R,
       M.spec.push_back(t[q][2]);
       M.val.push_back(t[q][3] * k);
     }
+    // rate terms of f: the reaction's rate leaves a (and b), enters c
+    const int rows[3] = {a, b, c};
+    const double sg[3] = {-k, -k, k};
+    for (int q = 0; q < 3; ++q) {
+      if (rows[q] < 0) continue;
+      M.rrow.push_back(rows[q]);
+      M.ra.push_back(a);
+      M.rb.push_back(b);
+      M.rk.push_back(sg[q]);
+    }
   }
-  for (auto &kv : h->mech.by_lanes) {
-    cudaFree(kv.second.d_tmeta);
-    cudaFree(kv.second.d_tval);
-  }
+  for (auto &kv : h->mech.by_lanes) kv.second.release();
   h->mech = std::move(M);
+  return CAMP_OK;
+}
+
+namespace camp {
+namespace {
+
+// Per-lane term lists of the handle's mechanism for Lc lanes per cell, padded
+// to the longest lane and laid out [term][lane]: the Jacobian terms of the
+// lane's slots (tmeta = (species + 1) | slot row << 11) and the rate terms of
+// the lane's rows (rmeta = (a + 1) | (b + 1) << 11 | e << 22, row sl + e Lc).
+cudaError_t mech_terms(Mechanism &mech, int Lc, const Schedule &S, MechTerms **out) {
+  auto it = mech.by_lanes.find(Lc);
+  if (it != mech.by_lanes.end()) {
+    *out = &it->second;
+    return cudaSuccess;
+  }
+  auto pad = [Lc](std::vector<std::vector<std::pair<double, int>>> &lane,
+                  std::vector<double> &val, std::vector<int> &meta) {
+    size_t M = 1;
+    for (auto &l : lane) M = std::max(M, l.size());
+    val.assign(M * Lc, 0.0);
+    meta.assign(M * Lc, 0);
+    for (int q = 0; q < Lc; ++q)
+      for (size_t p = 0; p < lane[q].size(); ++p) {
+        val[p * Lc + q] = lane[q][p].first;
+        meta[p * Lc + q] = lane[q][p].second;
+      }
+    return (int)M;
+  };
+  std::vector<std::vector<std::pair<double, int>>> lane(Lc), rlane(Lc);
+  for (size_t q = 0; q < mech.entry.size(); ++q) {
+    const int t = S.dst[mech.entry[q]];
+    lane[t % Lc].push_back({mech.val[q], (mech.spec[q] + 1) | ((t / Lc) << 11)});
+  }
+  for (size_t q = 0; q < mech.rrow.size(); ++q) {
+    const int row = mech.rrow[q];
+    rlane[row % Lc].push_back(
+        {mech.rk[q], (mech.ra[q] + 1) | ((mech.rb[q] + 1) << 11) | ((row / Lc) << 22)});
+  }
+  std::vector<double> tval, rval;
+  std::vector<int> tmeta, rmeta;
+  MechTerms T;
+  T.count = pad(lane, tval, tmeta);
+  T.rcount = pad(rlane, rval, rmeta);
+  cudaError_t e;
+  if ((e = upload(&T.d_tval, tval)) != cudaSuccess ||
+      (e = upload(&T.d_tmeta, tmeta)) != cudaSuccess ||
+      (e = upload(&T.d_rval, rval)) != cudaSuccess ||
+      (e = upload(&T.d_rmeta, rmeta)) != cudaSuccess) {
+    T.release();
+    return e;
+  }
+  *out = &mech.by_lanes.emplace(Lc, T).first->second;
+  return cudaSuccess;
+}
+
+}  // namespace
+}  // namespace camp
+
+// Launch arguments shared by the fused assembly and the Newton launches;
+// vectors = per-cell vectors in shared memory.  Returns CAMP_OK or the error.
+static camp_status fused_args(camp_solver_t h, int cells, int vectors, WarpArgs *pa, int *pE,
+                              int *pwpb, size_t *psmem) {
+  cudaError_t e = cudaSetDevice(h->device);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
+  View &v = h->fwd;
+  const int Lc = (h->arrangement == CAMP_ARR_WARP) ? h->lanes : auto_lanes(v.n, kAutoRowsPerLane);
+  const int E = Lc ? (v.n + Lc - 1) / Lc : 0;
+  if (Lc == 0 || E > 8)
+    return fail(CAMP_EUNSUPPORTED, "fused assembly supports at most 8 rows per lane (n=%d)", v.n);
+  Schedule *S = nullptr;
+  if ((e = view_schedule(v, Lc, &S)) != cudaSuccess) return cuda_fail(e, "schedule upload");
+  if (S->L > 2047) return fail(CAMP_EUNSUPPORTED, "more than 2047 slots per lane");
+  MechTerms *T = nullptr;
+  if ((e = mech_terms(h->mech, Lc, *S, &T)) != cudaSuccess) return cuda_fail(e, "mechanism upload");
+  int wpb = h->wpb > 0 ? h->wpb : 4;
+  int segA = 0, segV = 0, segStride = 0;
+  size_t smem = warp_smem(v, Lc, S->L, wpb, &segA, &segV, &segStride, vectors);
+  while (smem > h->smem_optin && wpb > 1)
+    smem = warp_smem(v, Lc, S->L, --wpb, &segA, &segV, &segStride, vectors);
+  if (smem > h->smem_optin) return fail(CAMP_EUNSUPPORTED, "cell does not fit in shared memory");
+  WarpArgs a = {};
+  a.cells = cells; a.n = v.n; a.nnz = v.nnz;
+  a.Lc = Lc; a.log2Lc = ilog2(Lc); a.k = 32 / Lc; a.L = S->L;
+  a.segA = segA; a.segV = segV; a.segStride = segStride;
+  a.ngroups = (cells + a.k - 1) / a.k;
+  a.sched = S->d_words; a.src = S->d_src;
+  a.dst = S->d_dst; a.padfrom = S->d_padfrom; a.dslot = S->d_dslot;
+  a.x0_given = 0;
+  a.queue = h->d_queue;
+  a.tval = T->d_tval; a.tmeta = T->d_tmeta; a.tcount = T->count;
+  a.rval = T->d_rval; a.rmeta = T->d_rmeta; a.rcount = T->rcount;
+  *pa = a;
+  *pE = E;
+  *pwpb = wpb;
+  *psmem = smem;
   return CAMP_OK;
 }
 
@@ -827,67 +938,61 @@ camp_status camp_solver_assemble_solve(camp_solver_t h, int cells,
   if (cells == 0) return CAMP_OK;
   if (!conc || !gamma || !b || !x || !iters_out || !resid_out)
     return fail(CAMP_EINVAL, "null array pointer");
-  cudaError_t e = cudaSetDevice(h->device);
-  if (e != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
-  View &v = h->fwd;
-  const int Lc = (h->arrangement == CAMP_ARR_WARP) ? h->lanes : auto_lanes(v.n, kAutoRowsPerLane);
-  const int E = Lc ? (v.n + Lc - 1) / Lc : 0;
-  if (Lc == 0 || E > 8)
-    return fail(CAMP_EUNSUPPORTED, "fused assembly supports at most 8 rows per lane (n=%d)", v.n);
-  Schedule *S = nullptr;
-  if ((e = view_schedule(v, Lc, &S)) != cudaSuccess) return cuda_fail(e, "schedule upload");
-  if (S->L > 2047) return fail(CAMP_EUNSUPPORTED, "more than 2047 slots per lane");
-  auto it = h->mech.by_lanes.find(Lc);
-  if (it == h->mech.by_lanes.end()) {
-    // every lane's terms (its slots' Jacobian terms, reaction order), padded
-    // to the longest lane and laid out [term][lane]
-    std::vector<std::vector<std::pair<double, int>>> lane(Lc);
-    for (size_t q = 0; q < h->mech.entry.size(); ++q) {
-      const int t = S->dst[h->mech.entry[q]];
-      lane[t % Lc].push_back({h->mech.val[q], (h->mech.spec[q] + 1) | ((t / Lc) << 11)});
-    }
-    size_t M = 1;
-    for (auto &l : lane) M = std::max(M, l.size());
-    std::vector<double> tval(M * Lc, 0.0);
-    std::vector<int> tmeta(M * Lc, 0);
-    for (int q = 0; q < Lc; ++q)
-      for (size_t p = 0; p < lane[q].size(); ++p) {
-        tval[p * Lc + q] = lane[q][p].first;
-        tmeta[p * Lc + q] = lane[q][p].second;
-      }
-    MechTerms T;
-    T.count = (int)M;
-    if ((e = upload(&T.d_tval, tval)) != cudaSuccess ||
-        (e = upload(&T.d_tmeta, tmeta)) != cudaSuccess) {
-      cudaFree(T.d_tval);
-      cudaFree(T.d_tmeta);
-      return cuda_fail(e, "mechanism upload");
-    }
-    it = h->mech.by_lanes.emplace(Lc, T).first;
-  }
-  int wpb = h->wpb > 0 ? h->wpb : 4;
-  int segA = 0, segV = 0, segStride = 0;
-  size_t smem = warp_smem(v, Lc, S->L, wpb, &segA, &segV, &segStride);
-  while (smem > h->smem_optin && wpb > 1) smem = warp_smem(v, Lc, S->L, --wpb, &segA, &segV, &segStride);
-  if (smem > h->smem_optin) return fail(CAMP_EUNSUPPORTED, "cell does not fit in shared memory");
-  WarpArgs a = {};
-  a.cells = cells; a.n = v.n; a.nnz = v.nnz;
-  a.Lc = Lc; a.log2Lc = ilog2(Lc); a.k = 32 / Lc; a.L = S->L;
-  a.segA = segA; a.segV = segV; a.segStride = segStride;
-  a.ngroups = (cells + a.k - 1) / a.k;
+  WarpArgs a;
+  int E = 0, wpb = 0;
+  size_t smem = 0;
+  camp_status rc = fused_args(h, cells, kWarpVectors, &a, &E, &wpb, &smem);
+  if (rc != CAMP_OK) return rc;
   a.A = nullptr; a.b = b; a.x = x; a.iters = iters_out; a.resid = resid_out;
-  a.status = status_out; a.sched = S->d_words; a.src = S->d_src;
-  a.dst = S->d_dst; a.padfrom = S->d_padfrom; a.dslot = S->d_dslot;
-  a.tol = tol; a.maxit = maxit; a.x0_given = 0;
-  a.queue = h->d_queue;
+  a.status = status_out;
+  a.tol = tol; a.maxit = maxit;
   a.conc = conc; a.gamma = gamma;
-  a.tval = it->second.d_tval; a.tmeta = it->second.d_tmeta; a.tcount = it->second.count;
   int occ = 0;
+  cudaError_t e;
   if ((e = assemble_occupancy(E, wpb, smem, &occ)) != cudaSuccess) return cuda_fail(e, "occupancy");
   if (occ < 1) occ = 1;
   const int grid = std::max(1, std::min((a.ngroups + wpb - 1) / wpb, h->sms * occ));
   if ((e = launch_assemble(E, a, wpb, grid, smem, h->stream)) != cudaSuccess)
     return cuda_fail(e, "assembly kernel launch");
+  return CAMP_OK;
+}
+
+camp_status camp_solver_newton_solve(camp_solver_t h, int cells,
+                                     const double *a_hist, const double *gamma,
+                                     double *y, double newton_tol, int max_newton,
+                                     double lin_tol, int lin_maxit,
+                                     int *newton_iters_out, int *lin_iters_out,
+                                     double *upd_out, double *resid_out,
+                                     int *status_out) {
+  if (!h) return fail(CAMP_EINVAL, "null solver handle");
+  if (cells < 0) return fail(CAMP_EINVAL, "cells < 0");
+  if (!(newton_tol > 0.0) || !std::isfinite(newton_tol))
+    return fail(CAMP_EINVAL, "newton_tol must be finite and > 0");
+  if (!(lin_tol > 0.0) || !std::isfinite(lin_tol))
+    return fail(CAMP_EINVAL, "lin_tol must be finite and > 0");
+  if (max_newton < 0) return fail(CAMP_EINVAL, "max_newton must be >= 0");
+  if (lin_maxit < 1) return fail(CAMP_EINVAL, "lin_maxit must be >= 1");
+  if (cells == 0) return CAMP_OK;
+  if (!a_hist || !gamma || !y || !newton_iters_out || !lin_iters_out || !upd_out || !resid_out)
+    return fail(CAMP_EINVAL, "null array pointer");
+  WarpArgs a;
+  int E = 0, wpb = 0;
+  size_t smem = 0;
+  camp_status rc = fused_args(h, cells, kWarpVectors + 1, &a, &E, &wpb, &smem);
+  if (rc != CAMP_OK) return rc;
+  a.A = nullptr; a.b = a_hist; a.x = y; a.iters = lin_iters_out; a.resid = resid_out;
+  a.status = status_out;
+  a.tol = lin_tol; a.maxit = lin_maxit;
+  a.conc = nullptr; a.gamma = gamma;
+  a.newton_tol = newton_tol; a.max_newton = max_newton;
+  a.newton_iters = newton_iters_out; a.upd = upd_out;
+  int occ = 0;
+  cudaError_t e;
+  if ((e = newton_occupancy(E, wpb, smem, &occ)) != cudaSuccess) return cuda_fail(e, "occupancy");
+  if (occ < 1) occ = 1;
+  const int grid = std::max(1, std::min((a.ngroups + wpb - 1) / wpb, h->sms * occ));
+  if ((e = launch_newton(E, a, wpb, grid, smem, h->stream)) != cudaSuccess)
+    return cuda_fail(e, "Newton kernel launch");
   return CAMP_OK;
 }
 

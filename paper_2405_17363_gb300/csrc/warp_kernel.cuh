@@ -60,7 +60,111 @@ __device__ __forceinline__ void ssum3(double &a, double &b, double &c, int Lc) {
 // solve_group): staged from A into shared memory in slot order, read from A
 // through L1 by the SpMV, or assembled in shared memory from the cell's
 // concentrations (A = I - gamma J).
-constexpr int kSrcStaged = 0, kSrcGlobal = 1, kSrcAssembled = 2;
+constexpr int kSrcStaged = 0, kSrcGlobal = 1, kSrcAssembled = 2, kSrcNewton = 3;
+
+// Newton corrector of the implicit step G(y) = y - gamma f(y) - a = 0 for
+// the segment's cell (a: history term in b; y: initial guess in x, replaced
+// by the solution): each iteration evaluates the mass-action rates f(y),
+// sets the right-hand side -G(y), assembles A = I - gamma J(y) and solves
+// A d = -G(y) through stage_and_solve, then y += d; converged when
+// ||d|| <= newton_tol ||y||.  Status 0 converged, 1 iterations exhausted,
+// 2 linear solve failed, 3 non-finite; iters = BiCGSTAB iterations summed.
+template <int E, class Solve>
+__device__ __forceinline__ void newton_loop(const WarpArgs &a, bool has, bool &live, int c,
+                                            int sl, int Lc, int n, double *o1, double *o2,
+                                            double *nrh, double (&xv)[E], int &st, int &it,
+                                            double &resid, Solve &stage_and_solve) {
+  double y[E];
+#pragma unroll
+  for (int e = 0; e < E; ++e) {
+    const int i = sl + e * Lc;
+    y[e] = (has && i < n) ? a.x[(size_t)c * n + i] : 0.0;
+  }
+  const double gam = has ? __ldg(a.gamma + c) : 0.0;
+  const double nt2 = a.newton_tol * a.newton_tol;
+  const bool any = a.max_newton > 0;
+  int nst = has ? (any ? -1 : 1) : 0, nit = 0, lin = 0;
+  double upd = 0.0, lres = 0.0;
+  bool act = has && any;
+  while (__any_sync(kFull, act)) {
+    // the iterate to the concentration buffer, f(y) accumulated in o1 (each
+    // lane adds the terms of its own rows)
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+      o2[sl + e * Lc] = y[e];
+      o1[sl + e * Lc] = 0.0;
+    }
+    __syncwarp();
+    const double *rv = a.rval + sl;
+    const int *rm = a.rmeta + sl;
+    for (int q = 0; q < a.rcount; ++q) {
+      const int meta = __ldg(rm + q * Lc);
+      const int ya = (meta & 0x7ff) - 1, yb = ((meta >> 11) & 0x7ff) - 1;
+      const int row = sl + ((meta >> 22) & 0xff) * Lc;
+      double term = __ldg(rv + q * Lc) * (ya >= 0 ? o2[ya] : 1.0);
+      if (yb >= 0) term *= o2[yb];
+      o1[row] += term;
+    }
+    // right-hand side -G(y) = a - (y - gamma f(y))
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+      const int i = sl + e * Lc;
+      const double ai = (act && i < n) ? __ldg(a.b + (size_t)c * n + i) : 0.0;
+      nrh[i] = ai - fma(-gam, o1[i], y[e]);
+    }
+    __syncwarp();
+    live = act;
+    stage_and_solve();
+    const bool ok = act && st == CAMP_CELL_CONVERGED;
+    double d2 = 0.0, y2 = 0.0;
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+      if (ok) y[e] += xv[e];
+      d2 = fma(xv[e], xv[e], d2);
+      y2 = fma(y[e], y[e], y2);
+    }
+    d2 = seg_sum_exact(d2, Lc);
+    y2 = seg_sum_exact(y2, Lc);
+    if (act) {
+      ++nit;
+      lin += it;
+      lres = resid;
+      if (!ok) {
+        nst = (st == CAMP_CELL_NONFINITE) ? 3 : 2;
+        act = false;
+      } else if (!is_finite_bits(d2) || !is_finite_bits(y2)) {
+        nst = 3;
+        act = false;
+      } else {
+        // ||d|| <= tol ||y|| (||d|| <= tol when y = 0) on the squares
+        const bool y0 = is_zero_bits(y2);
+        upd = y0 ? sqrt(d2) : sqrt(d2 * recip64(y2));
+        if (le_nonneg(d2, y0 ? nt2 : nt2 * y2)) {
+          nst = 0;
+          act = false;
+        } else if (nit >= a.max_newton) {
+          nst = 1;
+          act = false;
+        }
+      }
+    }
+  }
+  if (has) {
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+      const int i = sl + e * Lc;
+      if (i < n) a.x[(size_t)c * n + i] = y[e];
+    }
+    if (sl == 0) {
+      a.newton_iters[c] = nit;
+      a.iters[c] = lin;
+      a.upd[c] = upd;
+      a.resid[c] = lres;
+      if (a.status) a.status[c] = nst;
+    }
+  }
+  __syncwarp();
+}
 
 // Solve the k = 32/Lc cells of group g (cells g*k .. g*k+k-1) of one
 // mechanism with this warp.  wbase: the warp's shared-memory region; sch: this
@@ -80,6 +184,7 @@ __device__ __forceinline__ void solve_group(const WarpArgs &a, int g,
   double *o2 = o1 + a.segV;      // t = A s^
   double *rhs = o2 + a.segV;     // shadow residual r^
   double *dvs = rhs + a.segV;    // Jacobi reciprocals
+  double *nrh = dvs + a.segV;    // Newton right-hand side (Newton launch only)
   const int pos = g * a.k + seg;
   const bool has = pos < a.cells;
   const int c = (has && a.order) ? __ldg(a.order + pos) : pos;
@@ -88,20 +193,34 @@ __device__ __forceinline__ void solve_group(const WarpArgs &a, int g,
     if (ASMEM) seg_spmv(sch, a.L, Lc, Asl, gs, out);                 \
     else seg_spmv_gather(sch, srcl, a.L, Lc, Ac, gs, out);           \
   } while (0)
-  // ---- stage the cell's matrix values in slot order (Sec. 3.1: one cell,
-  // one team); the transposed view's permutation is folded into src
   const double *Ac = a.A + (size_t)(has ? c : 0) * nnz;
   const int *srcl = a.src + sl;
   const int LL = a.L * Lc;
   constexpr bool ASMEM = SRC != kSrcGlobal;
-  if (SRC == kSrcAssembled) {
+  const double *Asl = Abase + sl;  // this lane's slots (stride Lc)
+  double xv[E];
+  int st = -1, it = 0;
+  double resid = 0.0;
+  bool live = has;  // the cell takes part in the next solve
+  // Stage (or assemble) the cell's matrix and run BiCGSTAB on it: x in xv,
+  // status, iterations and true relative residual in st, it, resid.  The
+  // right-hand side comes from b, or from nrh in the Newton launch; a segment
+  // whose cell is not live only follows the warp's shuffles.
+  auto stage_and_solve = [&]() {
+  st = -1;
+  it = 0;
+  resid = 0.0;
+  // ---- stage the cell's matrix values in slot order (Sec. 3.1: one cell,
+  // one team); the transposed view's permutation is folded into src
+  if (SRC == kSrcAssembled || SRC == kSrcNewton) {
     // J accumulates in place in the lane's own slots, then A = I - gamma J
     for (int t = sl; t < LL; t += Lc) Abase[t] = 0.0;
     // the cell's concentrations go to the (not yet used) t-product buffer
-    if (has)
+    // (the Newton launch has put the current iterate there)
+    if (SRC == kSrcAssembled && live)
       for (int i = sl; i < n; i += Lc) o2[i] = __ldg(a.conc + (size_t)c * n + i);
     __syncwarp();
-    const double gam = has ? __ldg(a.gamma + c) : 0.0;
+    const double gam = live ? __ldg(a.gamma + c) : 0.0;
     const double *tv = a.tval + sl;
     const int *tm = a.tmeta + sl;
     for (int p = 0; p < a.tcount; ++p) {
@@ -118,10 +237,9 @@ __device__ __forceinline__ void solve_group(const WarpArgs &a, int g,
   } else if (ASMEM) {
     // coalesced read of the cell's A row, scattered into slot order; each lane
     // zeroes its own padding slots (never a scatter target)
-    for (int k = sl; k < nnz; k += Lc) Abase[__ldg(a.dst + k)] = has ? __ldg(Ac + k) : 0.0;
+    for (int k = sl; k < nnz; k += Lc) Abase[__ldg(a.dst + k)] = live ? __ldg(Ac + k) : 0.0;
     for (int t = __ldg(a.padfrom + sl) * Lc + sl; t < LL; t += Lc) Abase[t] = 0.0;
   }
-  const double *Asl = Abase + sl;  // this lane's slots (stride Lc)
   // pad rows of the product vectors are never written by the SpMV
   for (int i = n + sl; i < E * Lc; i += Lc) {
     o1[i] = 0.0;
@@ -129,15 +247,15 @@ __device__ __forceinline__ void solve_group(const WarpArgs &a, int g,
   }
   __syncwarp();
 
-  double r[E], p[E], xv[E], s[E];
+  double r[E], p[E], s[E];
   double bb;
   {
     double acc[1] = {0.0};
 #pragma unroll
     for (int e = 0; e < E; ++e) {
       const int i = sl + e * Lc;
-      const bool v = has && i < n;
-      const double bi = v ? __ldg(a.b + (size_t)c * n + i) : 0.0;
+      const bool v = live && i < n;
+      const double bi = v ? (SRC == kSrcNewton ? nrh[i] : __ldg(a.b + (size_t)c * n + i)) : 0.0;
       const double d = v ? (ASMEM ? Abase[__ldg(a.dslot + i)]
                                : __ldg(Ac + __ldg(a.src + __ldg(a.dslot + i)))) : 0.0;
       dvs[i] = v ? (!is_zero_bits(d) ? recip64(d) : 1.0) : 0.0;
@@ -150,10 +268,9 @@ __device__ __forceinline__ void solve_group(const WarpArgs &a, int g,
     bb = ssum1(acc[0], Lc);
   }
   const double thr = (tol * tol) * bb;  // (tol ||b||)^2
-  int st = -1, it = 0, nbreak = 0;
-  double resid = 0.0;
-  bool done = !has;
-  if (has) {
+  int nbreak = 0;
+  bool done = !live;
+  if (live) {
     if (!is_finite_bits(bb)) {
       st = CAMP_CELL_NONFINITE;
       resid = __longlong_as_double(0x7ff8000000000000ll);
@@ -266,7 +383,7 @@ __device__ __forceinline__ void solve_group(const WarpArgs &a, int g,
       bool full = false;
       if (active) {
         if (le_nonneg(q0, thr)) {
-          active = false;  // converged on the half step (x has alpha p^)
+          active = false;  // converged on the half step (x live alpha p^)
         } else if (!is_finite_bits(q1) || !is_finite_bits(q2)) {
           nonfin = true;
           active = false;
@@ -318,7 +435,7 @@ __device__ __forceinline__ void solve_group(const WarpArgs &a, int g,
 #pragma unroll
     for (int e = 0; e < E; ++e) {
       const int i = sl + e * Lc;
-      const double bi = (has && i < n) ? __ldg(a.b + (size_t)c * n + i) : 0.0;
+      const double bi = (live && i < n) ? (SRC == kSrcNewton ? nrh[i] : __ldg(a.b + (size_t)c * n + i)) : 0.0;
       s[e] = bi - o1[i];  // s holds the true residual here
       rt2[0] = fma(s[e], s[e], rt2[0]);
     }
@@ -342,6 +459,14 @@ __device__ __forceinline__ void solve_group(const WarpArgs &a, int g,
     }
     if (!__any_sync(kFull, restart)) break;
   }
+  };  // stage_and_solve
+
+  if (SRC == kSrcNewton) {
+    newton_loop<E>(a, has, live, c, sl, Lc, n, o1, o2, nrh, xv, st, it, resid,
+                   stage_and_solve);
+    return;
+  }
+  stage_and_solve();
   // ---- write the cell's results
   if (has) {
 #pragma unroll
@@ -402,6 +527,13 @@ template <int E>
 __global__ void __launch_bounds__(256, CAMP_WARP_MINB)
     warp_bicgstab_kernel(const WarpArgs a) {
   plain_launch_body<E, kSrcStaged>(a);
+}
+
+// Device Newton corrector of the implicit step around the assembly + solve.
+template <int E>
+__global__ void __launch_bounds__(256, CAMP_WARP_MINB)
+    newton_bicgstab_kernel(const WarpArgs a) {
+  plain_launch_body<E, kSrcNewton>(a);
 }
 
 // Fused Jacobian assembly and solve (A = I - gamma J(conc) built per cell).
