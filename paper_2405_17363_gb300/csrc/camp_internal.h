@@ -14,8 +14,18 @@ namespace camp {
 //   sum is stored to row.  Alongside, src[j][sl] is the entry of the cell's
 //   A row (pattern order) that slot uses, or -1 for padding: each cell's A is
 //   staged in slot order, so lanes read consecutive shared-memory words.
+//
+// Each lane's slots form kSpmvTracks tracks of H = L / kSpmvTracks slots
+// (track r holds slots r*H .. r*H + H - 1), each a run of whole rows: the
+// SpMV walks the tracks side by side with one running sum each, so a lane
+// has kSpmvTracks independent chains of multiply-adds in flight.  The
+// padding of track r starts at padfrom[r][sl].
 typedef unsigned int SchedWord;
 constexpr unsigned kSlotEnd = 0x80000000u;
+#ifndef CAMP_SPMV_TRACKS
+#define CAMP_SPMV_TRACKS 1
+#endif
+constexpr int kSpmvTracks = CAMP_SPMV_TRACKS;
 // Bytes the plain launches reserve at the start of dynamic shared memory for
 // nsch schedule words (rounded to 16); the host sizes the allocation and the
 // kernels place their per-warp regions with this one function.
@@ -41,7 +51,7 @@ struct WarpArgs {
   const SchedWord *sched;  // [L x Lc] slot words
   const int *src;          // [L x Lc] A entry of each slot (transposed view: permuted), -1 pad
   const int *dst;          // [nnz] slot of each A entry (pattern order): inverse of src
-  const int *padfrom;      // [Lc] first padding slot of each lane
+  const int *padfrom;      // [tracks][Lc] first padding slot of each lane's track
   const int *dslot;        // [n] slot of each row's diagonal entry
   double tol;
   int maxit;
@@ -150,9 +160,13 @@ constexpr int kMaxE = 16;  // rows per lane supported by the warp kernel
 // (kernel, device): setting the attribute on every launch serialises
 // otherwise-concurrent work on some drivers.
 cudaError_t ensure_max_smem(const void *kernel);
-// vectors of n (padded) doubles per cell in the warp kernel's shared memory:
-// gathered vector, two products, shadow residual, Jacobi reciprocals
-constexpr int kWarpVectors = 5;
+// Vectors of n (padded) doubles per cell in the warp kernel's shared memory
+// for E rows per lane: the gathered vector and the two products; up to
+// kRegVecMaxE rows per lane the shadow residual and the Jacobi reciprocals
+// stay in registers (freeing shared memory for more resident warps), beyond
+// it they take two more vectors.  The Newton launch adds one vector.
+constexpr int kRegVecMaxE = 5;
+__host__ __device__ constexpr int warp_vectors(int E) { return E <= kRegVecMaxE ? 3 : 5; }
 
 }  // namespace camp
 

@@ -48,17 +48,12 @@ __global__ void __launch_bounds__(256, 2) mixed_refine_kernel(const MixedArgs a)
     const bool has = c < a.cells;
     {  // stage A in slot order, FP64 and its FP32 rounding
       const double *Ac = a.A + (size_t)(has ? c : 0) * nnz;
-      const int LL = a.L * Lc;
-      for (int k = sl; k < nnz; k += Lc) {
-        const double v = has ? __ldg(Ac + k) : 0.0;
-        const int t = __ldg(a.dst + k);
+      stage_scatter(Ac, a.dst, nnz, sl, Lc, has, [&](int t, double v) {
         As[t] = v;
         As32[t] = d2f_rn(v);
-      }
-      for (int t = __ldg(a.padfrom + sl) * Lc + sl; t < LL; t += Lc) {
-        As[t] = 0.0;
-        As32[t] = 0.0f;
-      }
+      });
+      zero_padding(As, a.padfrom, a.L, Lc, sl);
+      zero_padding(As32, a.padfrom, a.L, Lc, sl);
     }
     __syncwarp();
     double xv[E];

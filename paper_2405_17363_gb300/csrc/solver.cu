@@ -139,33 +139,38 @@ struct Schedule {
 Schedule build_schedule(int n, const std::vector<int> &rp,
                         const std::vector<int> &ci, const std::vector<int> &perm,
                         const std::vector<int> &diag, int Lc) {
+  // longest rows first into the least-loaded of kSpmvTracks * Lc bins; bin b
+  // is track b / Lc of lane b % Lc
+  const int B = kSpmvTracks * Lc;
   std::vector<int> order(n);
   std::iota(order.begin(), order.end(), 0);
   std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
     return (rp[a + 1] - rp[a]) > (rp[b + 1] - rp[b]);
   });
-  std::vector<long> load(Lc, 0);
-  std::vector<std::vector<int>> rows(Lc);
+  std::vector<long> load(B, 0);
+  std::vector<std::vector<int>> rows(B);
   for (int r : order) {
     int best = 0;
-    for (int q = 1; q < Lc; ++q)
+    for (int q = 1; q < B; ++q)
       if (load[q] < load[best]) best = q;
     load[best] += rp[r + 1] - rp[r];
     rows[best].push_back(r);
   }
   Schedule S;
   S.Lc = Lc;
-  S.L = (int)*std::max_element(load.begin(), load.end());
+  const int H = (int)*std::max_element(load.begin(), load.end());
+  S.L = kSpmvTracks * H;
   S.words.assign((size_t)S.L * Lc, 0u);
   S.src.assign((size_t)S.L * Lc, -1);
   S.dslot.assign(n, -1);
   S.dst.assign(rp[n], -1);
-  S.padfrom.assign(Lc, 0);
-  for (int q = 0; q < Lc; ++q) {
-    S.padfrom[q] = (int)load[q];
-    std::sort(rows[q].begin(), rows[q].end());
-    int j = 0;
-    for (int r : rows[q])
+  S.padfrom.assign(B, 0);
+  for (int b = 0; b < B; ++b) {
+    const int q = b % Lc, track = b / Lc;
+    S.padfrom[b] = track * H + (int)load[b];
+    std::sort(rows[b].begin(), rows[b].end());
+    int j = track * H;
+    for (int r : rows[b])
       for (int k = rp[r]; k < rp[r + 1]; ++k, ++j) {
         const size_t t = (size_t)j * Lc + q;
         S.words[t] = (unsigned)ci[k] | ((unsigned)r << 11) |
@@ -316,12 +321,12 @@ int bank_spread_stride(int need, int k) {
 
 // Warp kernel shared-memory bytes for one CTA.
 size_t warp_smem(const View &v, int Lc, int L, int wpb, int *segA, int *segV,
-                 int *segStride, int vectors = kWarpVectors) {
+                 int *segStride, int extra_vectors = 0) {
   const int k = 32 / Lc;
   const int E = (v.n + Lc - 1) / Lc;
   *segA = (L * Lc + 1) & ~1;  // A in slot order
   *segV = ((E * Lc + 1) + 1) & ~1;
-  *segStride = bank_spread_stride(*segA + vectors * *segV, k);
+  *segStride = bank_spread_stride(*segA + (warp_vectors(E) + extra_vectors) * *segV, k);
   const size_t sch = sched_smem_bytes(L * Lc);
   return sch + (size_t)wpb * k * (size_t)*segStride * 8;
 }
@@ -887,8 +892,8 @@ cudaError_t mech_terms(Mechanism &mech, int Lc, const Schedule &S, MechTerms **o
 }  // namespace camp
 
 // Launch arguments shared by the fused assembly and the Newton launches;
-// vectors = per-cell vectors in shared memory.  Returns CAMP_OK or the error.
-static camp_status fused_args(camp_solver_t h, int cells, int vectors, WarpArgs *pa, int *pE,
+// extra_vectors = shared vectors per cell beyond the solve's own.  Returns CAMP_OK or the error.
+static camp_status fused_args(camp_solver_t h, int cells, int extra_vectors, WarpArgs *pa, int *pE,
                               int *pwpb, size_t *psmem) {
   cudaError_t e = cudaSetDevice(h->device);
   if (e != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
@@ -904,9 +909,9 @@ static camp_status fused_args(camp_solver_t h, int cells, int vectors, WarpArgs 
   if ((e = mech_terms(h->mech, Lc, *S, &T)) != cudaSuccess) return cuda_fail(e, "mechanism upload");
   int wpb = h->wpb > 0 ? h->wpb : 4;
   int segA = 0, segV = 0, segStride = 0;
-  size_t smem = warp_smem(v, Lc, S->L, wpb, &segA, &segV, &segStride, vectors);
+  size_t smem = warp_smem(v, Lc, S->L, wpb, &segA, &segV, &segStride, extra_vectors);
   while (smem > h->smem_optin && wpb > 1)
-    smem = warp_smem(v, Lc, S->L, --wpb, &segA, &segV, &segStride, vectors);
+    smem = warp_smem(v, Lc, S->L, --wpb, &segA, &segV, &segStride, extra_vectors);
   if (smem > h->smem_optin) return fail(CAMP_EUNSUPPORTED, "cell does not fit in shared memory");
   WarpArgs a = {};
   a.cells = cells; a.n = v.n; a.nnz = v.nnz;
@@ -941,7 +946,7 @@ camp_status camp_solver_assemble_solve(camp_solver_t h, int cells,
   WarpArgs a;
   int E = 0, wpb = 0;
   size_t smem = 0;
-  camp_status rc = fused_args(h, cells, kWarpVectors, &a, &E, &wpb, &smem);
+  camp_status rc = fused_args(h, cells, 0, &a, &E, &wpb, &smem);
   if (rc != CAMP_OK) return rc;
   a.A = nullptr; a.b = b; a.x = x; a.iters = iters_out; a.resid = resid_out;
   a.status = status_out;
@@ -978,7 +983,7 @@ camp_status camp_solver_newton_solve(camp_solver_t h, int cells,
   WarpArgs a;
   int E = 0, wpb = 0;
   size_t smem = 0;
-  camp_status rc = fused_args(h, cells, kWarpVectors + 1, &a, &E, &wpb, &smem);
+  camp_status rc = fused_args(h, cells, 1, &a, &E, &wpb, &smem);
   if (rc != CAMP_OK) return rc;
   a.A = nullptr; a.b = a_hist; a.x = y; a.iters = lin_iters_out; a.resid = resid_out;
   a.status = status_out;
@@ -1179,7 +1184,7 @@ camp_status camp_batch_solve(camp_batch_t b, const int *cells,
     a.Lc = Lc; a.log2Lc = ilog2(Lc); a.k = 32 / Lc; a.L = S->L;
     a.segA = asmem ? ((S->L * Lc + 1) & ~1) : 0;
     a.segV = ((E * Lc + 1) + 1) & ~1;
-    a.segStride = bank_spread_stride(a.segA + kWarpVectors * a.segV, a.k);
+    a.segStride = bank_spread_stride(a.segA + warp_vectors(E) * a.segV, a.k);
     a.ngroups = (cells[m] + a.k - 1) / a.k;
     a.A = A_vals[m]; a.b = bvec[m]; a.x = x[m]; a.iters = iters_out[m];
     a.resid = resid_out[m]; a.status = status_out ? status_out[m] : nullptr;
@@ -1275,10 +1280,10 @@ std::mutex g_noalloc_mu;                              // guards the host buffers
 void *g_noalloc_dev[kNoAllocMaxDevices];              // device address of the scratch
 SchedWord g_noalloc_words[kNoAllocScratchBytes / sizeof(SchedWord)];
 int g_noalloc_dst[kNoAllocScratchBytes / sizeof(int)];
-int g_noalloc_padfrom[32];
+int g_noalloc_padfrom[kSpmvTracks * 32];
 int g_noalloc_order[1024], g_noalloc_diag[1024], g_noalloc_dslot[1024];
-int g_noalloc_bin_rows[32][1024], g_noalloc_bin_count[32];
-long g_noalloc_load[32];
+int g_noalloc_bin_rows[kSpmvTracks * 32][1024], g_noalloc_bin_count[kSpmvTracks * 32];
+long g_noalloc_load[kSpmvTracks * 32];
 
 // Same schedule as build_schedule (longest-first bin packing of whole rows,
 // ties to the lower lane, rows ascending within a lane), written into the
@@ -1297,27 +1302,30 @@ int noalloc_schedule(int n, const int *rp, const int *ci, int Lc, size_t cap_slo
     }
     g_noalloc_order[j + 1] = r;
   }
-  for (int q = 0; q < Lc; ++q) {
+  const int B = kSpmvTracks * Lc;  // bin b: track b / Lc of lane b % Lc
+  for (int q = 0; q < B; ++q) {
     g_noalloc_load[q] = 0;
     g_noalloc_bin_count[q] = 0;
   }
   for (int i = 0; i < n; ++i) {
     const int r = g_noalloc_order[i];
     int best = 0;
-    for (int q = 1; q < Lc; ++q)
+    for (int q = 1; q < B; ++q)
       if (g_noalloc_load[q] < g_noalloc_load[best]) best = q;
     g_noalloc_load[best] += rp[r + 1] - rp[r];
     g_noalloc_bin_rows[best][g_noalloc_bin_count[best]++] = r;
   }
-  long L = 0;
-  for (int q = 0; q < Lc; ++q) L = std::max(L, g_noalloc_load[q]);
+  long H = 0;
+  for (int q = 0; q < B; ++q) H = std::max(H, g_noalloc_load[q]);
+  const long L = kSpmvTracks * H;
   if ((size_t)L * Lc > cap_slots) return -1;
   for (long w = 0; w < L * Lc; ++w) g_noalloc_words[w] = 0u;
-  for (int q = 0; q < Lc; ++q) {
-    g_noalloc_padfrom[q] = (int)g_noalloc_load[q];
-    int *rows = g_noalloc_bin_rows[q];
-    const int cnt = g_noalloc_bin_count[q];
-    for (int i = 1; i < cnt; ++i) {  // ascending row order within the lane
+  for (int b = 0; b < B; ++b) {
+    const int q = b % Lc, track = b / Lc;
+    g_noalloc_padfrom[b] = (int)(track * H + g_noalloc_load[b]);
+    int *rows = g_noalloc_bin_rows[b];
+    const int cnt = g_noalloc_bin_count[b];
+    for (int i = 1; i < cnt; ++i) {  // ascending row order within the bin
       const int r = rows[i];
       int j = i - 1;
       while (j >= 0 && rows[j] > r) {
@@ -1326,7 +1334,7 @@ int noalloc_schedule(int n, const int *rp, const int *ci, int Lc, size_t cap_slo
       }
       rows[j + 1] = r;
     }
-    long j = 0;
+    long j = track * H;
     for (int t = 0; t < cnt; ++t) {
       const int r = rows[t];
       for (int k = rp[r]; k < rp[r + 1]; ++k, ++j) {
@@ -1381,10 +1389,11 @@ camp_status camp_solve_noalloc(int n, int nnz, const int *row_ptr,
     if (g_noalloc_diag[i] < 0) return fail(CAMP_EPATTERN, "diagonal entry missing in row %d", i);
   }
   // scratch layout, 16-byte aligned pieces: [diagonal slots, n ints]
-  // [first padding slot per lane, 32 ints][slot of every entry, nnz ints]
+  // [first padding slot per lane and track, tracks x 32 ints][slot of every
+  // entry, nnz ints]
   // [slot words, L*Lc]
   const size_t diag_bytes = ((size_t)n * sizeof(int) + 15) & ~(size_t)15;
-  const size_t pad_bytes = 32 * sizeof(int);
+  const size_t pad_bytes = kSpmvTracks * 32 * sizeof(int);
   const size_t dst_bytes = ((size_t)nnz * sizeof(int) + 15) & ~(size_t)15;
   const size_t head_bytes = diag_bytes + pad_bytes + dst_bytes;
   const size_t cap_slots = head_bytes < kNoAllocScratchBytes
@@ -1418,7 +1427,7 @@ camp_status camp_solve_noalloc(int n, int nnz, const int *row_ptr,
   a.Lc = Lc; a.log2Lc = ilog2(Lc); a.k = 32 / Lc; a.L = L;
   a.segA = (L * Lc + 1) & ~1;
   a.segV = ((E * Lc + 1) + 1) & ~1;
-  a.segStride = bank_spread_stride(a.segA + kWarpVectors * a.segV, a.k);
+  a.segStride = bank_spread_stride(a.segA + warp_vectors(E) * a.segV, a.k);
   a.ngroups = (cells + a.k - 1) / a.k;
   a.A = A_vals; a.b = b; a.x = x; a.iters = iters_out; a.resid = resid_out;
   a.status = status_out;
@@ -1442,7 +1451,7 @@ camp_status camp_solve_noalloc(int n, int nnz, const int *row_ptr,
   // host buffer has been consumed)
   if ((e = cudaMemcpyAsync(scratch, g_noalloc_dslot, (size_t)n * sizeof(int),
                            cudaMemcpyHostToDevice, st)) != cudaSuccess ||
-      (e = cudaMemcpyAsync(scratch + diag_bytes, g_noalloc_padfrom, (size_t)Lc * sizeof(int),
+      (e = cudaMemcpyAsync(scratch + diag_bytes, g_noalloc_padfrom, (size_t)kSpmvTracks * Lc * sizeof(int),
                            cudaMemcpyHostToDevice, st)) != cudaSuccess ||
       (e = cudaMemcpyAsync(scratch + diag_bytes + pad_bytes, g_noalloc_dst,
                            (size_t)nnz * sizeof(int), cudaMemcpyHostToDevice, st)) != cudaSuccess ||

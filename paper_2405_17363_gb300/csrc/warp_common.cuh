@@ -88,22 +88,40 @@ __device__ __forceinline__ void seg_sum3(double &a, double &b, double &c, int Lc
 }
 
 // o[row] = sum over this lane's slots of A_slot * g[col].  sch and As point at
-// this lane's column of the schedule and of the slot-ordered A (stride Lc).
+// this lane's column of the schedule and of the slot-ordered A (stride Lc);
+// the kSpmvTracks tracks are walked side by side.
+__device__ __forceinline__ double fma_t(double a, double b, double c) { return fma(a, b, c); }
+__device__ __forceinline__ float fma_t(float a, float b, float c) { return fmaf(a, b, c); }
+
+template <class T, class LoadA>
+__device__ __forceinline__ void spmv_tracks(const SchedWord *__restrict__ sch, int L, int Lc,
+                                            LoadA loadA, const T *__restrict__ gs,
+                                            T *__restrict__ os) {
+  const int H = L / kSpmvTracks;
+  T acc[kSpmvTracks];
+#pragma unroll
+  for (int r = 0; r < kSpmvTracks; ++r) acc[r] = T(0);
+#pragma unroll kSpmvUnroll
+  for (int j = 0; j < H; ++j) {
+#pragma unroll
+    for (int r = 0; r < kSpmvTracks; ++r) {
+      const int jj = j + r * H;
+      const SchedWord w = sch[jj * Lc];
+      acc[r] = fma_t(loadA(jj), gs[w & 0x7ffu], acc[r]);
+      if (w & kSlotEnd) {
+        os[(w >> 11) & 0x7ffu] = acc[r];
+        acc[r] = T(0);
+      }
+    }
+  }
+}
+
 __device__ __forceinline__ void seg_spmv(const SchedWord *__restrict__ sch,
                                          int L, int Lc,
                                          const double *__restrict__ As,
                                          const double *__restrict__ gs,
                                          double *__restrict__ os) {
-  double acc = 0.0;
-#pragma unroll kSpmvUnroll
-  for (int j = 0; j < L; ++j) {
-    const SchedWord w = sch[j * Lc];
-    acc = fma(As[j * Lc], gs[w & 0x7ffu], acc);
-    if (w & kSlotEnd) {
-      os[(w >> 11) & 0x7ffu] = acc;
-      acc = 0.0;
-    }
-  }
+  spmv_tracks<double>(sch, L, Lc, [&](int j) { return As[j * Lc]; }, gs, os);
 }
 
 // Same with A read from global memory through the slot's source entry.
@@ -113,17 +131,45 @@ __device__ __forceinline__ void seg_spmv_gather(const SchedWord *__restrict__ sc
                                                 const double *__restrict__ Ag,
                                                 const double *__restrict__ gs,
                                                 double *__restrict__ os) {
-  double acc = 0.0;
-#pragma unroll kSpmvUnroll
-  for (int j = 0; j < L; ++j) {
-    const SchedWord w = sch[j * Lc];
+  spmv_tracks<double>(sch, L, Lc, [&](int j) {
     const int k = __ldg(src + j * Lc);
-    acc = fma(k >= 0 ? __ldg(Ag + k) : 0.0, gs[w & 0x7ffu], acc);
-    if (w & kSlotEnd) {
-      os[(w >> 11) & 0x7ffu] = acc;
-      acc = 0.0;
+    return k >= 0 ? __ldg(Ag + k) : 0.0;
+  }, gs, os);
+}
+
+// Coalesced read of one cell's A row (CSR order, lane sl reads entries
+// sl, sl + Lc, ...) handed to put(slot, value) with the slot from the dst map.
+// The loads are issued kStageBatch at a time before any store, so a lane
+// waits for memory once per batch rather than once per entry.
+constexpr int kStageBatch = 16;
+template <class Put>
+__device__ __forceinline__ void stage_scatter(const double *__restrict__ Ac,
+                                              const int *__restrict__ dst, int nnz,
+                                              int sl, int Lc, bool live, Put put) {
+  for (int k0 = sl; k0 < nnz; k0 += kStageBatch * Lc) {
+    double v[kStageBatch];
+    int d[kStageBatch];
+#pragma unroll
+    for (int u = 0; u < kStageBatch; ++u) {
+      const int k = k0 + u * Lc;
+      d[u] = k < nnz ? __ldg(dst + k) : -1;
+      v[u] = (live && k < nnz) ? __ldg(Ac + k) : 0.0;
     }
+#pragma unroll
+    for (int u = 0; u < kStageBatch; ++u)
+      if (d[u] >= 0) put(d[u], v[u]);
   }
+}
+
+// Zero this lane's padding slots of a slot-ordered A (never scatter targets).
+template <class T>
+__device__ __forceinline__ void zero_padding(T *__restrict__ Abase, const int *__restrict__ padfrom,
+                                             int L, int Lc, int sl) {
+  const int H = L / kSpmvTracks;
+#pragma unroll
+  for (int r = 0; r < kSpmvTracks; ++r)
+    for (int t = __ldg(padfrom + r * Lc + sl) * Lc + sl; t < (r + 1) * H * Lc; t += Lc)
+      Abase[t] = T(0);
 }
 
 // float variant of the segment sum
@@ -141,16 +187,7 @@ __device__ __forceinline__ void seg_spmvf(const SchedWord *__restrict__ sch,
                                           const float *__restrict__ As,
                                           const float *__restrict__ gs,
                                           float *__restrict__ os) {
-  float acc = 0.0f;
-#pragma unroll kSpmvUnroll
-  for (int j = 0; j < L; ++j) {
-    const SchedWord w = sch[j * Lc];
-    acc = fmaf(As[j * Lc], gs[w & 0x7ffu], acc);
-    if (w & kSlotEnd) {
-      os[(w >> 11) & 0x7ffu] = acc;
-      acc = 0.0f;
-    }
-  }
+  spmv_tracks<float>(sch, L, Lc, [&](int j) { return As[j * Lc]; }, gs, os);
 }
 
 // FP64 -> FP32 conversion, round to nearest even, entirely on the integer

@@ -9,8 +9,10 @@
 // lanes; every FP64 instruction is issued once for all k cells of the warp.
 //
 // Shared memory per cell: its matrix values A_s [segA] (unless read through
-// L1 from global memory), the gathered vector g_s, the products o1_s = A p^
-// and o2_s = A s^, the shadow residual and the Jacobi reciprocals [segV each].
+// L1 from global memory), the gathered vector g_s and the products o1_s = A p^
+// and o2_s = A s^ [segV each]; the shadow residual and the Jacobi reciprocals
+// are lane-local and stay in registers up to kRegVecMaxE rows per lane (two
+// more shared vectors beyond).
 // The plain launch also keeps the SpMV schedule in shared memory; the
 // persistent launch (several mechanisms) reads each mechanism's schedule
 // through L1.
@@ -61,6 +63,23 @@ __device__ __forceinline__ void ssum3(double &a, double &b, double &c, int Lc) {
 // through L1 by the SpMV, or assembled in shared memory from the cell's
 // concentrations (A = I - gamma J).
 constexpr int kSrcStaged = 0, kSrcGlobal = 1, kSrcAssembled = 2, kSrcNewton = 3;
+
+// A lane's rows e = 0..E-1 of a per-cell vector: in registers, or in the
+// cell's shared-memory vector (element sl + e*Lc).
+template <int E, bool REG>
+struct LaneRows;
+template <int E>
+struct LaneRows<E, true> {
+  double v[E];
+  __device__ __forceinline__ double &operator[](int e) { return v[e]; }
+};
+template <int E>
+struct LaneRows<E, false> {
+  double *p;
+  int Lc;
+  __device__ __forceinline__ void bind(double *q, int lc) { p = q; Lc = lc; }
+  __device__ __forceinline__ double &operator[](int e) { return p[e * Lc]; }
+};
 
 // Newton corrector of the implicit step G(y) = y - gamma f(y) - a = 0 for
 // the segment's cell (a: history term in b; y: initial guess in x, replaced
@@ -182,9 +201,13 @@ __device__ __forceinline__ void solve_group(const WarpArgs &a, int g,
   double *gs = Abase + a.segA;   // gathered vector (p^, s^ or x)
   double *o1 = gs + a.segV;      // v = A p^
   double *o2 = o1 + a.segV;      // t = A s^
-  double *rhs = o2 + a.segV;     // shadow residual r^
-  double *dvs = rhs + a.segV;    // Jacobi reciprocals
-  double *nrh = dvs + a.segV;    // Newton right-hand side (Newton launch only)
+  constexpr bool kVR = E <= kRegVecMaxE;
+  LaneRows<E, kVR> rhs, dvs;     // shadow residual r^, Jacobi reciprocals
+  if constexpr (!kVR) {
+    rhs.bind(o2 + a.segV + sl, Lc);
+    dvs.bind(o2 + 2 * a.segV + sl, Lc);
+  }
+  double *nrh = o2 + (kVR ? 1 : 3) * a.segV;  // Newton right-hand side
   const int pos = g * a.k + seg;
   const bool has = pos < a.cells;
   const int c = (has && a.order) ? __ldg(a.order + pos) : pos;
@@ -237,8 +260,8 @@ __device__ __forceinline__ void solve_group(const WarpArgs &a, int g,
   } else if (ASMEM) {
     // coalesced read of the cell's A row, scattered into slot order; each lane
     // zeroes its own padding slots (never a scatter target)
-    for (int k = sl; k < nnz; k += Lc) Abase[__ldg(a.dst + k)] = live ? __ldg(Ac + k) : 0.0;
-    for (int t = __ldg(a.padfrom + sl) * Lc + sl; t < LL; t += Lc) Abase[t] = 0.0;
+    stage_scatter(Ac, a.dst, nnz, sl, Lc, live, [&](int t, double v) { Abase[t] = v; });
+    zero_padding(Abase, a.padfrom, a.L, Lc, sl);
   }
   // pad rows of the product vectors are never written by the SpMV
   for (int i = n + sl; i < E * Lc; i += Lc) {
@@ -258,7 +281,7 @@ __device__ __forceinline__ void solve_group(const WarpArgs &a, int g,
       const double bi = v ? (SRC == kSrcNewton ? nrh[i] : __ldg(a.b + (size_t)c * n + i)) : 0.0;
       const double d = v ? (ASMEM ? Abase[__ldg(a.dslot + i)]
                                : __ldg(Ac + __ldg(a.src + __ldg(a.dslot + i)))) : 0.0;
-      dvs[i] = v ? (!is_zero_bits(d) ? recip64(d) : 1.0) : 0.0;
+      dvs[e] = v ? (!is_zero_bits(d) ? recip64(d) : 1.0) : 0.0;
       xv[e] = (v && a.x0_given) ? a.x[(size_t)c * n + i] : 0.0;
       r[e] = bi;
       p[e] = 0.0;
@@ -304,7 +327,7 @@ __device__ __forceinline__ void solve_group(const WarpArgs &a, int g,
       if (restart) {
 #pragma unroll
         for (int e = 0; e < E; ++e) {
-          rhs[sl + e * Lc] = r[e];
+          rhs[e] = r[e];
           p[e] = 0.0;
         }
         rho = acc[0];
@@ -335,7 +358,7 @@ __device__ __forceinline__ void solve_group(const WarpArgs &a, int g,
       for (int e = 0; e < E; ++e) {
         const int i = sl + e * Lc;
         if (active) p[e] = fma(beta, p[e], r[e]);
-        gs[i] = dvs[i] * p[e];
+        gs[i] = dvs[e] * p[e];
       }
       __syncwarp();
       SPMV(o1);  // v = A p^
@@ -345,7 +368,7 @@ __device__ __forceinline__ void solve_group(const WarpArgs &a, int g,
 #pragma unroll
       for (int e = 0; e < E; ++e) {
         const int i = sl + e * Lc;
-        sg[0] = fma(rhs[i], o1[i], sg[0]);
+        sg[0] = fma(rhs[e], o1[i], sg[0]);
       }
       sg[0] = ssum1(sg[0], Lc);
       if (active) {
@@ -366,7 +389,7 @@ __device__ __forceinline__ void solve_group(const WarpArgs &a, int g,
           xv[e] = fma(al, gs[i], xv[e]);
           s[e] = fma(-al, o1[i], r[e]);
         }
-        gs[i] = dvs[i] * s[e];
+        gs[i] = dvs[e] * s[e];
       }
       __syncwarp();
       SPMV(o2);  // t = A s^
@@ -408,7 +431,7 @@ __device__ __forceinline__ void solve_group(const WarpArgs &a, int g,
       double hr = 0.0, rr = 0.0;
 #pragma unroll
       for (int e = 0; e < E; ++e) {
-        hr = fma(rhs[sl + e * Lc], r[e], hr);
+        hr = fma(rhs[e], r[e], hr);
         rr = fma(r[e], r[e], rr);
       }
       ssum2(hr, rr, Lc);
