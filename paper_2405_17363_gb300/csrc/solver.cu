@@ -29,6 +29,14 @@ CAMP_DECLM(1) CAMP_DECLM(2) CAMP_DECLM(3) CAMP_DECLM(4) CAMP_DECLM(5)
 CAMP_DECLM(6) CAMP_DECLM(7) CAMP_DECLM(8) CAMP_DECLM(9) CAMP_DECLM(10)
 CAMP_DECLM(11) CAMP_DECLM(12) CAMP_DECLM(13) CAMP_DECLM(14) CAMP_DECLM(15)
 CAMP_DECLM(16)
+#define CAMP_DECLF(E)                                                         \
+  cudaError_t launch_assemble_##E(const WarpArgs &, int, int, size_t, cudaStream_t); \
+  cudaError_t occ_assemble_##E(int, size_t, int *);                            \
+  cudaError_t launch_newton_##E(const WarpArgs &, int, int, size_t, cudaStream_t);   \
+  cudaError_t occ_newton_##E(int, size_t, int *);
+CAMP_DECLF(1) CAMP_DECLF(2) CAMP_DECLF(3) CAMP_DECLF(4) CAMP_DECLF(5)
+CAMP_DECLF(6) CAMP_DECLF(7) CAMP_DECLF(8)
+#undef CAMP_DECLF
 #undef CAMP_DECLM
 #undef CAMP_DECL
 
@@ -71,6 +79,42 @@ cudaError_t mixed_occupancy(int E, int wpb, size_t smem, int *blocks) {
     default: return cudaErrorInvalidValue;
   }
 }
+
+#define CAMP_DISPATCH8(fn, name)                                              \
+  cudaError_t fn(int E, const WarpArgs &a, int wpb, int grid, size_t smem,      \
+                 cudaStream_t st) {                                             \
+    switch (E) {                                                                \
+      case 1: return launch_##name##_1(a, wpb, grid, smem, st);                 \
+      case 2: return launch_##name##_2(a, wpb, grid, smem, st);                 \
+      case 3: return launch_##name##_3(a, wpb, grid, smem, st);                 \
+      case 4: return launch_##name##_4(a, wpb, grid, smem, st);                 \
+      case 5: return launch_##name##_5(a, wpb, grid, smem, st);                 \
+      case 6: return launch_##name##_6(a, wpb, grid, smem, st);                 \
+      case 7: return launch_##name##_7(a, wpb, grid, smem, st);                 \
+      case 8: return launch_##name##_8(a, wpb, grid, smem, st);                 \
+      default: return cudaErrorInvalidValue;                                    \
+    }                                                                           \
+  }
+#define CAMP_OCCUPANCY8(fn, name)                                             \
+  cudaError_t fn(int E, int wpb, size_t smem, int *blocks) {                    \
+    switch (E) {                                                                \
+      case 1: return occ_##name##_1(wpb, smem, blocks);                         \
+      case 2: return occ_##name##_2(wpb, smem, blocks);                         \
+      case 3: return occ_##name##_3(wpb, smem, blocks);                         \
+      case 4: return occ_##name##_4(wpb, smem, blocks);                         \
+      case 5: return occ_##name##_5(wpb, smem, blocks);                         \
+      case 6: return occ_##name##_6(wpb, smem, blocks);                         \
+      case 7: return occ_##name##_7(wpb, smem, blocks);                         \
+      case 8: return occ_##name##_8(wpb, smem, blocks);                         \
+      default: return cudaErrorInvalidValue;                                    \
+    }                                                                           \
+  }
+CAMP_DISPATCH8(launch_assemble, assemble)
+CAMP_OCCUPANCY8(assemble_occupancy, assemble)
+CAMP_DISPATCH8(launch_newton, newton)
+CAMP_OCCUPANCY8(newton_occupancy, newton)
+#undef CAMP_DISPATCH8
+#undef CAMP_OCCUPANCY8
 
 constexpr int kHostChunks = 8;        // pipeline depth of camp_solver_solve_host
 constexpr int kHostSolveStreams = 4;  // concurrent chunk solves
@@ -466,7 +510,7 @@ camp_status do_solve(camp_solver_t h, int cells, const double *A_vals,
 extern "C" {
 
 const char *camp_last_error(void) { return g_err.c_str(); }
-const char *camp_version(void) { return "campsolve 0.7 (sm_103a)"; }
+const char *camp_version(void) { return "campsolve 0.8 (sm_103a)"; }
 
 camp_status camp_schedule_build(int n, int nnz, const int *row_ptr,
                                 const int *col_idx, int lanes_per_cell,

@@ -310,4 +310,48 @@ __device__ __forceinline__ double seg_sum_exact(double v, int Lc) {
   return __longlong_as_double((long long)out);
 }
 
+// The same sum with the segment reductions done by redux.sync (one warp
+// instruction per reduction over the segment's lanes): the exponent maximum
+// directly, and the 64-bit fixed-point total as three 32-bit partial sums of
+// its 20-bit digits (16..32 lanes of 20-bit digits cannot overflow 32 bits),
+// recombined exactly.  Bit-identical to the shuffle version.
+__device__ __forceinline__ unsigned seg_mask(int Lc) {
+  const int lane = threadIdx.x & 31;
+  return Lc >= 32 ? 0xffffffffu : (((1u << Lc) - 1u) << (lane & ~(Lc - 1)));
+}
+__device__ __forceinline__ double seg_sum_exact_redux(double v, int Lc) {
+  const unsigned mask = seg_mask(Lc);
+  const unsigned long long u = (unsigned long long)__double_as_longlong(v);
+  const int e = (int)((u >> 52) & 0x7ffull);
+  const unsigned long long frac = u & 0xfffffffffffffull;
+  const unsigned long long m = e ? (frac | (1ull << 52)) : frac;
+  const int ee = e ? e : 1;
+  const int emax = (int)__reduce_max_sync(mask, (unsigned)ee);
+  const int sh = emax - ee;
+  long long f = sh >= 58 ? 0ll : (long long)((m << 5) >> sh);
+  f = (u >> 63) ? -f : f;
+  const unsigned d0 = (unsigned)(f & 0xfffffll);
+  const unsigned d1 = (unsigned)((f >> 20) & 0xfffffll);
+  const int d2 = (int)(f >> 40);
+  const unsigned s0 = __reduce_add_sync(mask, d0);
+  const unsigned s1 = __reduce_add_sync(mask, d1);
+  const int s2 = __reduce_add_sync(mask, d2);
+  f = ((long long)s2 << 40) + ((long long)s1 << 20) + (long long)s0;
+  const unsigned long long neg = f < 0 ? 1ull : 0ull;
+  const unsigned long long a = (unsigned long long)(f < 0 ? -f : f);
+  const int lz = __clzll((long long)a);
+  const unsigned long long an = a << (lz & 63);
+  unsigned long long mant = an >> 11;
+  const unsigned rem = (unsigned)(an & 0x7ffull);
+  mant += (rem > 0x400u || (rem == 0x400u && (mant & 1ull))) ? 1ull : 0ull;
+  int E = (63 - lz) + emax - 57;
+  E += (mant >> 53) ? 1 : 0;
+  mant = (mant >> 53) ? (mant >> 1) : mant;
+  unsigned long long out = (neg << 63) | ((unsigned long long)E << 52) | (mant & 0xfffffffffffffull);
+  out = (E <= 0 || a == 0ull) ? (neg << 63) : out;
+  out = (E >= 0x7ff) ? ((neg << 63) | (0x7ffull << 52)) : out;
+  out = (emax == 0x7ff) ? 0x7ff8000000000000ull : out;
+  return __longlong_as_double((long long)out);
+}
+
 }  // namespace camp

@@ -22,6 +22,7 @@
 // s and r, true-residual check with residual replacement, breakdown and
 // non-finite rules, iteration count = products v = A p^).
 #pragma once
+#include <type_traits>
 #include "warp_common.cuh"
 
 namespace camp {
@@ -30,25 +31,31 @@ namespace camp {
 #define CAMP_EXACT_SUMS 1  // segment sums on the integer pipe (0: FP64 shuffle tree)
 #endif
 
+#ifndef CAMP_REDUX_SUMS
+#define CAMP_REDUX_SUMS 0
+#endif
+__device__ __forceinline__ double xsum(double v, int Lc) {
+  return CAMP_REDUX_SUMS ? seg_sum_exact_redux(v, Lc) : seg_sum_exact(v, Lc);
+}
 __device__ __forceinline__ double ssum1(double v, int Lc) {
-  if (CAMP_EXACT_SUMS) return seg_sum_exact(v, Lc);
+  if (CAMP_EXACT_SUMS) return xsum(v, Lc);
   double a[1] = {v};
   seg_sum<1>(a, Lc);
   return a[0];
 }
 __device__ __forceinline__ void ssum2(double &a, double &b, int Lc) {
   if (CAMP_EXACT_SUMS) {
-    a = seg_sum_exact(a, Lc);
-    b = seg_sum_exact(b, Lc);
+    a = xsum(a, Lc);
+    b = xsum(b, Lc);
   } else {
     seg_sum2(a, b, Lc);
   }
 }
 __device__ __forceinline__ void ssum3(double &a, double &b, double &c, int Lc) {
   if (CAMP_EXACT_SUMS) {
-    a = seg_sum_exact(a, Lc);
-    b = seg_sum_exact(b, Lc);
-    c = seg_sum_exact(c, Lc);
+    a = xsum(a, Lc);
+    b = xsum(b, Lc);
+    c = xsum(c, Lc);
   } else {
     seg_sum3(a, b, c, Lc);
   }
@@ -188,14 +195,15 @@ __device__ __forceinline__ void newton_loop(const WarpArgs &a, bool has, bool &l
 // Solve the k = 32/Lc cells of group g (cells g*k .. g*k+k-1) of one
 // mechanism with this warp.  wbase: the warp's shared-memory region; sch: this
 // lane's column of the SpMV schedule (shared or global memory).
-template <int E, int SRC>
+template <int E, int SRC, int LC = 0>
 __device__ __forceinline__ void solve_group(const WarpArgs &a, int g,
                                             double *wbase,
                                             const SchedWord *sch) {
   const int lane = threadIdx.x & 31;
-  const int seg = lane >> a.log2Lc;
-  const int sl = lane & (a.Lc - 1);
-  const int n = a.n, nnz = a.nnz, Lc = a.Lc;
+  const int Lc = LC ? LC : a.Lc;   // lanes per cell (compile-time when LC > 0)
+  const int seg = LC ? lane / LC : lane >> a.log2Lc;
+  const int sl = lane & (Lc - 1);
+  const int n = a.n, nnz = a.nnz;
   const double tol = a.tol;
   double *Abase = wbase + (size_t)seg * a.segStride;
   double *gs = Abase + a.segA;   // gathered vector (p^, s^ or x)
@@ -208,7 +216,7 @@ __device__ __forceinline__ void solve_group(const WarpArgs &a, int g,
     dvs.bind(o2 + 2 * a.segV + sl, Lc);
   }
   double *nrh = o2 + (kVR ? 1 : 3) * a.segV;  // Newton right-hand side
-  const int pos = g * a.k + seg;
+  const int pos = g * (LC ? 32 / LC : a.k) + seg;
   const bool has = pos < a.cells;
   const int c = (has && a.order) ? __ldg(a.order + pos) : pos;
 #define SPMV(out)                                                    \
@@ -522,19 +530,34 @@ __device__ __forceinline__ void plain_launch_body(const WarpArgs &a) {
                   (size_t)warp * a.k * a.segStride;
   const SchedWord *sch = sch_s + (lane & (a.Lc - 1));
   const int warps_total = gridDim.x * (blockDim.x >> 5);
-  if (!a.queue) {
-    for (int g = blockIdx.x * (blockDim.x >> 5) + warp; g < a.ngroups; g += warps_total)
-      solve_group<E, SRC>(a, g, wbase, sch);
-    return;
+  auto run = [&](auto lc) {
+    constexpr int LC = decltype(lc)::value;
+    if (!a.queue) {
+      for (int g = blockIdx.x * (blockDim.x >> 5) + warp; g < a.ngroups; g += warps_total)
+        solve_group<E, SRC, LC>(a, g, wbase, sch);
+      return;
+    }
+    // dynamic assignment: warps take the next group until none is left
+    for (;;) {
+      unsigned g = 0;
+      if (lane == 0) g = atomicAdd(a.queue, 1u);
+      g = __shfl_sync(kFull, g, 0);
+      if (g >= (unsigned)a.ngroups) break;
+      solve_group<E, SRC, LC>(a, (int)g, wbase, sch);
+    }
+  };
+  // The arrangements the automatic choice makes for 21..160 rows (3 to 5 rows
+  // per lane on 8, 16 or 32 lanes) run code with Lc fixed at compile time:
+  // constant strides fold into the shared-memory addressing.
+  if constexpr (E >= 3 && E <= kRegVecMaxE) {
+    if (a.Lc == 16) run(std::integral_constant<int, 16>());
+    else if (a.Lc == 32) run(std::integral_constant<int, 32>());
+    else if (a.Lc == 8) run(std::integral_constant<int, 8>());
+    else run(std::integral_constant<int, 0>());
+  } else {
+    run(std::integral_constant<int, 0>());
   }
-  // dynamic assignment: warps take the next group until none is left
-  for (;;) {
-    unsigned g = 0;
-    if (lane == 0) g = atomicAdd(a.queue, 1u);
-    g = __shfl_sync(kFull, g, 0);
-    if (g >= (unsigned)a.ngroups) break;
-    solve_group<E, SRC>(a, (int)g, wbase, sch);
-  }
+  if (!a.queue) return;
   if (lane == 0) {
     // every other warp has taken its last group before counting itself done,
     // so the last one may reset the queue for the next launch
