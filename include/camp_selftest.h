@@ -14,8 +14,10 @@
  *         elements (the integer-pipe segment sum: every term aligned to the
  *         group's largest exponent with 5 guard bits, summed exactly, rounded
  *         once);
- *   op 4: the same sum by the FP64 shuffle tree.
- * For ops 3 and 4, n must be a multiple of 32 and lanes a power of two in
+ *   op 4: the same sum by the FP64 shuffle tree;
+ *   op 5: the op-3 sum with its reductions done by full-warp redux.sync
+ *         (bit-identical to op 3 by construction).
+ * For ops 3 to 5, n must be a multiple of 32 and lanes a power of two in
  * [1, 32].  Returns CAMP_EINVAL for bad arguments, CAMP_ECUDA if the launch
  * fails.  The paper has no counterpart: this is test support.
  */

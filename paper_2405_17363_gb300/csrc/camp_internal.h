@@ -14,18 +14,8 @@ namespace camp {
 //   sum is stored to row.  Alongside, src[j][sl] is the entry of the cell's
 //   A row (pattern order) that slot uses, or -1 for padding: each cell's A is
 //   staged in slot order, so lanes read consecutive shared-memory words.
-//
-// Each lane's slots form kSpmvTracks tracks of H = L / kSpmvTracks slots
-// (track r holds slots r*H .. r*H + H - 1), each a run of whole rows: the
-// SpMV walks the tracks side by side with one running sum each, so a lane
-// has kSpmvTracks independent chains of multiply-adds in flight.  The
-// padding of track r starts at padfrom[r][sl].
 typedef unsigned int SchedWord;
 constexpr unsigned kSlotEnd = 0x80000000u;
-#ifndef CAMP_SPMV_TRACKS
-#define CAMP_SPMV_TRACKS 1
-#endif
-constexpr int kSpmvTracks = CAMP_SPMV_TRACKS;
 // Bytes the plain launches reserve at the start of dynamic shared memory for
 // nsch schedule words (rounded to 16); the host sizes the allocation and the
 // kernels place their per-warp regions with this one function.
@@ -51,7 +41,7 @@ struct WarpArgs {
   const SchedWord *sched;  // [L x Lc] slot words
   const int *src;          // [L x Lc] A entry of each slot (transposed view: permuted), -1 pad
   const int *dst;          // [nnz] slot of each A entry (pattern order): inverse of src
-  const int *padfrom;      // [tracks][Lc] first padding slot of each lane's track
+  const int *padfrom;      // [Lc] first padding slot of each lane
   const int *dslot;        // [n] slot of each row's diagonal entry
   double tol;
   int maxit;

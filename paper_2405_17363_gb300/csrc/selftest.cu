@@ -19,6 +19,15 @@ __global__ void selftest_kernel(int op, int n, const double *in, double *out, in
     double a[1] = {v};
     seg_sum<1>(a, lanes);
     r = a[0];
+  } else if (op == 5) {  // the whole warp takes part
+    switch (lanes) {
+      case 1: r = seg_sum_exact_redux<32>(v); break;
+      case 2: r = seg_sum_exact_redux<16>(v); break;
+      case 4: r = seg_sum_exact_redux<8>(v); break;
+      case 8: r = seg_sum_exact_redux<4>(v); break;
+      case 16: r = seg_sum_exact_redux<2>(v); break;
+      default: r = seg_sum_exact_redux<1>(v); break;
+    }
   }
   if (ok) out[i] = r;
 }
@@ -28,7 +37,7 @@ __global__ void selftest_kernel(int op, int n, const double *in, double *out, in
 
 extern "C" camp_status camp_selftest(int op, int n, const double *in, double *out,
                                      int lanes, void *stream) {
-  if (op < 0 || op > 4 || n < 0 || !in || !out) return CAMP_EINVAL;
+  if (op < 0 || op > 5 || n < 0 || !in || !out) return CAMP_EINVAL;
   if (op >= 3 && (lanes < 1 || lanes > 32 || (lanes & (lanes - 1)) || n % 32)) return CAMP_EINVAL;
   if (n == 0) return CAMP_OK;
   camp::selftest_kernel<<<(n + 255) / 256, 256, 0, (cudaStream_t)stream>>>(op, n, in, out, lanes);

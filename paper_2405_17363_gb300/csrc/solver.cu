@@ -183,38 +183,34 @@ struct Schedule {
 Schedule build_schedule(int n, const std::vector<int> &rp,
                         const std::vector<int> &ci, const std::vector<int> &perm,
                         const std::vector<int> &diag, int Lc) {
-  // longest rows first into the least-loaded of kSpmvTracks * Lc bins; bin b
-  // is track b / Lc of lane b % Lc
-  const int B = kSpmvTracks * Lc;
+  // longest rows first onto the least-loaded lane
   std::vector<int> order(n);
   std::iota(order.begin(), order.end(), 0);
   std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
     return (rp[a + 1] - rp[a]) > (rp[b + 1] - rp[b]);
   });
-  std::vector<long> load(B, 0);
-  std::vector<std::vector<int>> rows(B);
+  std::vector<long> load(Lc, 0);
+  std::vector<std::vector<int>> rows(Lc);
   for (int r : order) {
     int best = 0;
-    for (int q = 1; q < B; ++q)
+    for (int q = 1; q < Lc; ++q)
       if (load[q] < load[best]) best = q;
     load[best] += rp[r + 1] - rp[r];
     rows[best].push_back(r);
   }
   Schedule S;
   S.Lc = Lc;
-  const int H = (int)*std::max_element(load.begin(), load.end());
-  S.L = kSpmvTracks * H;
+  S.L = (int)*std::max_element(load.begin(), load.end());
   S.words.assign((size_t)S.L * Lc, 0u);
   S.src.assign((size_t)S.L * Lc, -1);
   S.dslot.assign(n, -1);
   S.dst.assign(rp[n], -1);
-  S.padfrom.assign(B, 0);
-  for (int b = 0; b < B; ++b) {
-    const int q = b % Lc, track = b / Lc;
-    S.padfrom[b] = track * H + (int)load[b];
-    std::sort(rows[b].begin(), rows[b].end());
-    int j = track * H;
-    for (int r : rows[b])
+  S.padfrom.assign(Lc, 0);
+  for (int q = 0; q < Lc; ++q) {
+    S.padfrom[q] = (int)load[q];
+    std::sort(rows[q].begin(), rows[q].end());
+    int j = 0;
+    for (int r : rows[q])
       for (int k = rp[r]; k < rp[r + 1]; ++k, ++j) {
         const size_t t = (size_t)j * Lc + q;
         S.words[t] = (unsigned)ci[k] | ((unsigned)r << 11) |
@@ -510,7 +506,7 @@ camp_status do_solve(camp_solver_t h, int cells, const double *A_vals,
 extern "C" {
 
 const char *camp_last_error(void) { return g_err.c_str(); }
-const char *camp_version(void) { return "campsolve 0.8 (sm_103a)"; }
+const char *camp_version(void) { return "campsolve 0.9 (sm_103a)"; }
 
 camp_status camp_schedule_build(int n, int nnz, const int *row_ptr,
                                 const int *col_idx, int lanes_per_cell,
@@ -1324,10 +1320,10 @@ std::mutex g_noalloc_mu;                              // guards the host buffers
 void *g_noalloc_dev[kNoAllocMaxDevices];              // device address of the scratch
 SchedWord g_noalloc_words[kNoAllocScratchBytes / sizeof(SchedWord)];
 int g_noalloc_dst[kNoAllocScratchBytes / sizeof(int)];
-int g_noalloc_padfrom[kSpmvTracks * 32];
+int g_noalloc_padfrom[32];
 int g_noalloc_order[1024], g_noalloc_diag[1024], g_noalloc_dslot[1024];
-int g_noalloc_bin_rows[kSpmvTracks * 32][1024], g_noalloc_bin_count[kSpmvTracks * 32];
-long g_noalloc_load[kSpmvTracks * 32];
+int g_noalloc_bin_rows[32][1024], g_noalloc_bin_count[32];
+long g_noalloc_load[32];
 
 // Same schedule as build_schedule (longest-first bin packing of whole rows,
 // ties to the lower lane, rows ascending within a lane), written into the
@@ -1346,30 +1342,27 @@ int noalloc_schedule(int n, const int *rp, const int *ci, int Lc, size_t cap_slo
     }
     g_noalloc_order[j + 1] = r;
   }
-  const int B = kSpmvTracks * Lc;  // bin b: track b / Lc of lane b % Lc
-  for (int q = 0; q < B; ++q) {
+  for (int q = 0; q < Lc; ++q) {
     g_noalloc_load[q] = 0;
     g_noalloc_bin_count[q] = 0;
   }
   for (int i = 0; i < n; ++i) {
     const int r = g_noalloc_order[i];
     int best = 0;
-    for (int q = 1; q < B; ++q)
+    for (int q = 1; q < Lc; ++q)
       if (g_noalloc_load[q] < g_noalloc_load[best]) best = q;
     g_noalloc_load[best] += rp[r + 1] - rp[r];
     g_noalloc_bin_rows[best][g_noalloc_bin_count[best]++] = r;
   }
-  long H = 0;
-  for (int q = 0; q < B; ++q) H = std::max(H, g_noalloc_load[q]);
-  const long L = kSpmvTracks * H;
+  long L = 0;
+  for (int q = 0; q < Lc; ++q) L = std::max(L, g_noalloc_load[q]);
   if ((size_t)L * Lc > cap_slots) return -1;
   for (long w = 0; w < L * Lc; ++w) g_noalloc_words[w] = 0u;
-  for (int b = 0; b < B; ++b) {
-    const int q = b % Lc, track = b / Lc;
-    g_noalloc_padfrom[b] = (int)(track * H + g_noalloc_load[b]);
-    int *rows = g_noalloc_bin_rows[b];
-    const int cnt = g_noalloc_bin_count[b];
-    for (int i = 1; i < cnt; ++i) {  // ascending row order within the bin
+  for (int q = 0; q < Lc; ++q) {
+    g_noalloc_padfrom[q] = (int)g_noalloc_load[q];
+    int *rows = g_noalloc_bin_rows[q];
+    const int cnt = g_noalloc_bin_count[q];
+    for (int i = 1; i < cnt; ++i) {  // ascending row order within the lane
       const int r = rows[i];
       int j = i - 1;
       while (j >= 0 && rows[j] > r) {
@@ -1378,7 +1371,7 @@ int noalloc_schedule(int n, const int *rp, const int *ci, int Lc, size_t cap_slo
       }
       rows[j + 1] = r;
     }
-    long j = track * H;
+    long j = 0;
     for (int t = 0; t < cnt; ++t) {
       const int r = rows[t];
       for (int k = rp[r]; k < rp[r + 1]; ++k, ++j) {
@@ -1433,11 +1426,10 @@ camp_status camp_solve_noalloc(int n, int nnz, const int *row_ptr,
     if (g_noalloc_diag[i] < 0) return fail(CAMP_EPATTERN, "diagonal entry missing in row %d", i);
   }
   // scratch layout, 16-byte aligned pieces: [diagonal slots, n ints]
-  // [first padding slot per lane and track, tracks x 32 ints][slot of every
-  // entry, nnz ints]
+  // [first padding slot per lane, 32 ints][slot of every entry, nnz ints]
   // [slot words, L*Lc]
   const size_t diag_bytes = ((size_t)n * sizeof(int) + 15) & ~(size_t)15;
-  const size_t pad_bytes = kSpmvTracks * 32 * sizeof(int);
+  const size_t pad_bytes = 32 * sizeof(int);
   const size_t dst_bytes = ((size_t)nnz * sizeof(int) + 15) & ~(size_t)15;
   const size_t head_bytes = diag_bytes + pad_bytes + dst_bytes;
   const size_t cap_slots = head_bytes < kNoAllocScratchBytes
@@ -1495,7 +1487,7 @@ camp_status camp_solve_noalloc(int n, int nnz, const int *row_ptr,
   // host buffer has been consumed)
   if ((e = cudaMemcpyAsync(scratch, g_noalloc_dslot, (size_t)n * sizeof(int),
                            cudaMemcpyHostToDevice, st)) != cudaSuccess ||
-      (e = cudaMemcpyAsync(scratch + diag_bytes, g_noalloc_padfrom, (size_t)kSpmvTracks * Lc * sizeof(int),
+      (e = cudaMemcpyAsync(scratch + diag_bytes, g_noalloc_padfrom, (size_t)Lc * sizeof(int),
                            cudaMemcpyHostToDevice, st)) != cudaSuccess ||
       (e = cudaMemcpyAsync(scratch + diag_bytes + pad_bytes, g_noalloc_dst,
                            (size_t)nnz * sizeof(int), cudaMemcpyHostToDevice, st)) != cudaSuccess ||

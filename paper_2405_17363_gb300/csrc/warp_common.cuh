@@ -7,10 +7,7 @@
 namespace camp {
 
 constexpr unsigned kFull = 0xffffffffu;
-#ifndef CAMP_SPMV_UNROLL
-#define CAMP_SPMV_UNROLL 4
-#endif
-constexpr int kSpmvUnroll = CAMP_SPMV_UNROLL;  // schedule slots in flight per lane
+constexpr int kSpmvUnroll = 4;  // SpMV pipeline block (slots per lane)
 
 __device__ __forceinline__ bool is_finite_bits(double v) {
   const unsigned long long u = (unsigned long long)__double_as_longlong(v);
@@ -87,41 +84,70 @@ __device__ __forceinline__ void seg_sum3(double &a, double &b, double &c, int Lc
   a = va; b = vb; c = vc;
 }
 
-// o[row] = sum over this lane's slots of A_slot * g[col].  sch and As point at
-// this lane's column of the schedule and of the slot-ordered A (stride Lc);
-// the kSpmvTracks tracks are walked side by side.
 __device__ __forceinline__ double fma_t(double a, double b, double c) { return fma(a, b, c); }
 __device__ __forceinline__ float fma_t(float a, float b, float c) { return fmaf(a, b, c); }
 
+// *p = v when flag != 0, as one predicated shared-memory store (no branch)
+__device__ __forceinline__ void store_if(unsigned flag, double *p, double v) {
+  const unsigned a = (unsigned)__cvta_generic_to_shared(p);
+  asm volatile("{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %0, 0;\n\t@q st.shared.f64 [%1], %2;\n\t}"
+               :: "r"(flag), "r"(a), "d"(v) : "memory");
+}
+__device__ __forceinline__ void store_if(unsigned flag, float *p, float v) {
+  const unsigned a = (unsigned)__cvta_generic_to_shared(p);
+  asm volatile("{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %0, 0;\n\t@q st.shared.f32 [%1], %2;\n\t}"
+               :: "r"(flag), "r"(a), "f"(v) : "memory");
+}
+
+// os[row] = sum over this lane's slots of A_slot * gs[col] (os: shared
+// memory).  sch and loadA(j) give this lane's word and A value of slot j.
+// Software pipeline over blocks of P slots: the block's A values and gathers
+// (its words were read one block earlier) and the next block's words are
+// issued before the block's chain of multiply-adds, so the shared-memory
+// latency runs under the FP64 chain; a row end is a predicated store and a
+// select, without a branch.  Slots past L read word 0 and A = 0 (no row end
+// follows them).
 template <class T, class LoadA>
-__device__ __forceinline__ void spmv_tracks(const SchedWord *__restrict__ sch, int L, int Lc,
-                                            LoadA loadA, const T *__restrict__ gs,
-                                            T *__restrict__ os) {
-  const int H = L / kSpmvTracks;
-  T acc[kSpmvTracks];
+__device__ __forceinline__ void spmv_slots(const SchedWord *__restrict__ sch, int L, int Lc,
+                                           LoadA loadA, const T *__restrict__ gs,
+                                           T *__restrict__ os) {
+  constexpr int P = kSpmvUnroll;
+  SchedWord w[P];
 #pragma unroll
-  for (int r = 0; r < kSpmvTracks; ++r) acc[r] = T(0);
-#pragma unroll kSpmvUnroll
-  for (int j = 0; j < H; ++j) {
+  for (int u = 0; u < P; ++u) w[u] = u < L ? sch[u * Lc] : 0u;
+  T acc = T(0);
+  for (int j0 = 0; j0 < L; j0 += P) {
+    T av[P], xv[P];
+    SchedWord wn[P];
 #pragma unroll
-    for (int r = 0; r < kSpmvTracks; ++r) {
-      const int jj = j + r * H;
-      const SchedWord w = sch[jj * Lc];
-      acc[r] = fma_t(loadA(jj), gs[w & 0x7ffu], acc[r]);
-      if (w & kSlotEnd) {
-        os[(w >> 11) & 0x7ffu] = acc[r];
-        acc[r] = T(0);
-      }
+    for (int u = 0; u < P; ++u) {
+      av[u] = j0 + u < L ? loadA(j0 + u) : T(0);
+      xv[u] = gs[w[u] & 0x7ffu];
     }
+#pragma unroll
+    for (int u = 0; u < P; ++u) {
+      const int j = j0 + P + u;
+      wn[u] = j < L ? sch[j * Lc] : 0u;
+    }
+#pragma unroll
+    for (int u = 0; u < P; ++u) {
+      acc = fma_t(av[u], xv[u], acc);
+      store_if(w[u] & kSlotEnd, os + ((w[u] >> 11) & 0x7ffu), acc);
+      acc = (w[u] & kSlotEnd) ? T(0) : acc;
+    }
+#pragma unroll
+    for (int u = 0; u < P; ++u) w[u] = wn[u];
   }
 }
 
+// o[row] = sum over this lane's slots of A_slot * g[col].  sch and As point at
+// this lane's column of the schedule and of the slot-ordered A (stride Lc).
 __device__ __forceinline__ void seg_spmv(const SchedWord *__restrict__ sch,
                                          int L, int Lc,
                                          const double *__restrict__ As,
                                          const double *__restrict__ gs,
                                          double *__restrict__ os) {
-  spmv_tracks<double>(sch, L, Lc, [&](int j) { return As[j * Lc]; }, gs, os);
+  spmv_slots<double>(sch, L, Lc, [&](int j) { return As[j * Lc]; }, gs, os);
 }
 
 // Same with A read from global memory through the slot's source entry.
@@ -131,7 +157,7 @@ __device__ __forceinline__ void seg_spmv_gather(const SchedWord *__restrict__ sc
                                                 const double *__restrict__ Ag,
                                                 const double *__restrict__ gs,
                                                 double *__restrict__ os) {
-  spmv_tracks<double>(sch, L, Lc, [&](int j) {
+  spmv_slots<double>(sch, L, Lc, [&](int j) {
     const int k = __ldg(src + j * Lc);
     return k >= 0 ? __ldg(Ag + k) : 0.0;
   }, gs, os);
@@ -165,11 +191,7 @@ __device__ __forceinline__ void stage_scatter(const double *__restrict__ Ac,
 template <class T>
 __device__ __forceinline__ void zero_padding(T *__restrict__ Abase, const int *__restrict__ padfrom,
                                              int L, int Lc, int sl) {
-  const int H = L / kSpmvTracks;
-#pragma unroll
-  for (int r = 0; r < kSpmvTracks; ++r)
-    for (int t = __ldg(padfrom + r * Lc + sl) * Lc + sl; t < (r + 1) * H * Lc; t += Lc)
-      Abase[t] = T(0);
+  for (int t = __ldg(padfrom + sl) * Lc + sl; t < L * Lc; t += Lc) Abase[t] = T(0);
 }
 
 // float variant of the segment sum
@@ -187,7 +209,7 @@ __device__ __forceinline__ void seg_spmvf(const SchedWord *__restrict__ sch,
                                           const float *__restrict__ As,
                                           const float *__restrict__ gs,
                                           float *__restrict__ os) {
-  spmv_tracks<float>(sch, L, Lc, [&](int j) { return As[j * Lc]; }, gs, os);
+  spmv_slots<float>(sch, L, Lc, [&](int j) { return As[j * Lc]; }, gs, os);
 }
 
 // FP64 -> FP32 conversion, round to nearest even, entirely on the integer
@@ -310,32 +332,46 @@ __device__ __forceinline__ double seg_sum_exact(double v, int Lc) {
   return __longlong_as_double((long long)out);
 }
 
-// The same sum with the segment reductions done by redux.sync (one warp
-// instruction per reduction over the segment's lanes): the exponent maximum
-// directly, and the 64-bit fixed-point total as three 32-bit partial sums of
-// its 20-bit digits (16..32 lanes of 20-bit digits cannot overflow 32 bits),
-// recombined exactly.  Bit-identical to the shuffle version.
-__device__ __forceinline__ unsigned seg_mask(int Lc) {
-  const int lane = threadIdx.x & 31;
-  return Lc >= 32 ? 0xffffffffu : (((1u << Lc) - 1u) << (lane & ~(Lc - 1)));
-}
-__device__ __forceinline__ double seg_sum_exact_redux(double v, int Lc) {
-  const unsigned mask = seg_mask(Lc);
+// The same sum with the segment reductions done by full-warp redux.sync (one
+// instruction per reduction, all lanes taking part): for each of the K =
+// 32/Lc segments, the lanes of that segment contribute and the others add
+// the neutral element.  The exponent maximum is reduced directly and the
+// 64-bit fixed-point total as three 32-bit sums of its 20-bit digits (at
+// most 32 lanes of 20-bit digits cannot overflow 32 bits), recombined
+// exactly, so the result is bit-identical to seg_sum_exact.
+template <int K>
+__device__ __forceinline__ double seg_sum_exact_redux(double v) {
+  constexpr int Lc = 32 / K;
+  const int seg = (threadIdx.x & 31) / Lc;
   const unsigned long long u = (unsigned long long)__double_as_longlong(v);
   const int e = (int)((u >> 52) & 0x7ffull);
   const unsigned long long frac = u & 0xfffffffffffffull;
   const unsigned long long m = e ? (frac | (1ull << 52)) : frac;
   const int ee = e ? e : 1;
-  const int emax = (int)__reduce_max_sync(mask, (unsigned)ee);
+  int emax = 0;
+#pragma unroll
+  for (int s = 0; s < K; ++s) {
+    const int r = (int)__reduce_max_sync(kFull, seg == s ? (unsigned)ee : 0u);
+    emax = seg == s ? r : emax;
+  }
   const int sh = emax - ee;
   long long f = sh >= 58 ? 0ll : (long long)((m << 5) >> sh);
   f = (u >> 63) ? -f : f;
   const unsigned d0 = (unsigned)(f & 0xfffffll);
   const unsigned d1 = (unsigned)((f >> 20) & 0xfffffll);
   const int d2 = (int)(f >> 40);
-  const unsigned s0 = __reduce_add_sync(mask, d0);
-  const unsigned s1 = __reduce_add_sync(mask, d1);
-  const int s2 = __reduce_add_sync(mask, d2);
+  unsigned s0 = 0, s1 = 0;
+  int s2 = 0;
+#pragma unroll
+  for (int s = 0; s < K; ++s) {
+    const bool mine = seg == s;
+    const unsigned r0 = __reduce_add_sync(kFull, mine ? d0 : 0u);
+    const unsigned r1 = __reduce_add_sync(kFull, mine ? d1 : 0u);
+    const int r2 = __reduce_add_sync(kFull, mine ? d2 : 0);
+    s0 = mine ? r0 : s0;
+    s1 = mine ? r1 : s1;
+    s2 = mine ? r2 : s2;
+  }
   f = ((long long)s2 << 40) + ((long long)s1 << 20) + (long long)s0;
   const unsigned long long neg = f < 0 ? 1ull : 0ull;
   const unsigned long long a = (unsigned long long)(f < 0 ? -f : f);

@@ -31,31 +31,36 @@ namespace camp {
 #define CAMP_EXACT_SUMS 1  // segment sums on the integer pipe (0: FP64 shuffle tree)
 #endif
 
-#ifndef CAMP_REDUX_SUMS
-#define CAMP_REDUX_SUMS 0
-#endif
+// Exact segment sum.  With Lc known at compile time and at most two cells
+// per warp, the reductions run as full-warp redux.sync (one instruction each;
+// a redux over part of a warp measured several times slower than shuffles).
+template <int LC>
 __device__ __forceinline__ double xsum(double v, int Lc) {
-  return CAMP_REDUX_SUMS ? seg_sum_exact_redux(v, Lc) : seg_sum_exact(v, Lc);
+  if constexpr (LC >= 16) return seg_sum_exact_redux<32 / LC>(v);
+  else return seg_sum_exact(v, Lc);
 }
+template <int LC>
 __device__ __forceinline__ double ssum1(double v, int Lc) {
-  if (CAMP_EXACT_SUMS) return xsum(v, Lc);
+  if (CAMP_EXACT_SUMS) return xsum<LC>(v, Lc);
   double a[1] = {v};
   seg_sum<1>(a, Lc);
   return a[0];
 }
+template <int LC>
 __device__ __forceinline__ void ssum2(double &a, double &b, int Lc) {
   if (CAMP_EXACT_SUMS) {
-    a = xsum(a, Lc);
-    b = xsum(b, Lc);
+    a = xsum<LC>(a, Lc);
+    b = xsum<LC>(b, Lc);
   } else {
     seg_sum2(a, b, Lc);
   }
 }
+template <int LC>
 __device__ __forceinline__ void ssum3(double &a, double &b, double &c, int Lc) {
   if (CAMP_EXACT_SUMS) {
-    a = xsum(a, Lc);
-    b = xsum(b, Lc);
-    c = xsum(c, Lc);
+    a = xsum<LC>(a, Lc);
+    b = xsum<LC>(b, Lc);
+    c = xsum<LC>(c, Lc);
   } else {
     seg_sum3(a, b, c, Lc);
   }
@@ -296,7 +301,7 @@ __device__ __forceinline__ void solve_group(const WarpArgs &a, int g,
       s[e] = 0.0;
       acc[0] = fma(bi, bi, acc[0]);
     }
-    bb = ssum1(acc[0], Lc);
+    bb = ssum1<LC>(acc[0], Lc);
   }
   const double thr = (tol * tol) * bb;  // (tol ||b||)^2
   int nbreak = 0;
@@ -331,7 +336,7 @@ __device__ __forceinline__ void solve_group(const WarpArgs &a, int g,
       double acc[1] = {0.0};
 #pragma unroll
       for (int e = 0; e < E; ++e) acc[0] = fma(r[e], r[e], acc[0]);
-      acc[0] = ssum1(acc[0], Lc);
+      acc[0] = ssum1<LC>(acc[0], Lc);
       if (restart) {
 #pragma unroll
         for (int e = 0; e < E; ++e) {
@@ -378,7 +383,7 @@ __device__ __forceinline__ void solve_group(const WarpArgs &a, int g,
         const int i = sl + e * Lc;
         sg[0] = fma(rhs[e], o1[i], sg[0]);
       }
-      sg[0] = ssum1(sg[0], Lc);
+      sg[0] = ssum1<LC>(sg[0], Lc);
       if (active) {
         if (!is_finite_bits(sg[0])) {
           nonfin = true;
@@ -410,7 +415,7 @@ __device__ __forceinline__ void solve_group(const WarpArgs &a, int g,
         q1 = fma(t, s[e], q1);
         q2 = fma(t, t, q2);
       }
-      ssum3(q0, q1, q2, Lc);
+      ssum3<LC>(q0, q1, q2, Lc);
       bool full = false;
       if (active) {
         if (le_nonneg(q0, thr)) {
@@ -442,7 +447,7 @@ __device__ __forceinline__ void solve_group(const WarpArgs &a, int g,
         hr = fma(rhs[e], r[e], hr);
         rr = fma(r[e], r[e], rr);
       }
-      ssum2(hr, rr, Lc);
+      ssum2<LC>(hr, rr, Lc);
       if (full) {
         nbreak = 0;
         if (le_nonneg(rr, thr)) {
@@ -470,7 +475,7 @@ __device__ __forceinline__ void solve_group(const WarpArgs &a, int g,
       s[e] = bi - o1[i];  // s holds the true residual here
       rt2[0] = fma(s[e], s[e], rt2[0]);
     }
-    rt2[0] = ssum1(rt2[0], Lc);
+    rt2[0] = ssum1<LC>(rt2[0], Lc);
     if (fin) {
       fin = false;
       resid = sqrt(rt2[0] * recip64(bb));

@@ -75,6 +75,11 @@ def test_integer_segment_sum_is_exact_to_one_rounding(cuda, lanes):
         bound = np.spacing(abs(exact)) + lanes * np.abs(seg).max() * 2.0 ** -57
         assert np.all(y[s:s + lanes] == y[s]), "every lane gets the same bits"
         assert abs(y[s] - exact) <= bound
+    # the full-warp redux form gives the same bits, NaN and Inf included
+    x2 = x.copy()
+    x2[64:96] = np.r_[[np.inf, 1.0, np.nan, -2.0] * 8]
+    x2[96:128] = np.ldexp(rng.standard_normal(32), -1060)
+    np.testing.assert_array_equal(_run(5, x2, lanes).view(np.int64), _run(3, x2, lanes).view(np.int64))
     # the FP64 shuffle tree meets the classic pairwise-summation bound
     tree = _run(4, x, lanes)
     levels = int(np.log2(lanes))
