@@ -123,11 +123,13 @@ camp_status camp_solver_set_arrangement(camp_solver_t h, int arrangement,
 
 /*
  * Cell ordering for the warp arrangement: 0 (default) solves cells in index
- * order; 1 first estimates each cell's difficulty (the largest Jacobi-scaled
- * off-diagonal row sum, in FP32) and hands cells to warps hardest first, so
- * the cells that share a warp need similar iteration counts.  Results are
- * identical either way (a cell's solve does not depend on its neighbours);
- * ordering adds two small launches and device scratch of 8 bytes per cell
+ * order; 1 first estimates each cell's difficulty (the largest departure of
+ * a diagonal entry from one, max_i |A_ii - 1|, which for A = I - gamma J is
+ * gamma times the largest loss rate) and hands cells to warps hardest first,
+ * so the cells that share a warp need similar iteration counts and the last
+ * groups of the launch are short.  Results are identical either way (a
+ * cell's solve does not depend on its neighbours); ordering adds a memset
+ * and two small launches and device scratch of about 5 bytes per cell
  * (allocated on first use, grown on demand).
  */
 camp_status camp_solver_set_ordering(camp_solver_t h, int ordering);

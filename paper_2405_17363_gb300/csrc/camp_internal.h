@@ -138,11 +138,13 @@ cudaError_t launch_newton(int E, const WarpArgs &a, int warps_per_block,
                           int grid, size_t smem, cudaStream_t st);
 cudaError_t newton_occupancy(int E, int warps_per_block, size_t smem, int *blocks);
 cudaError_t launch_grad(const GradArgs &a, cudaStream_t st);
-// Difficulty ordering: keys[c] = max_i sum_{j != i} |A_ij| / |A_ii| in FP32,
-// then order = cells by decreasing key (bucketed on log2 of the key).
+// Difficulty ordering: cells binned by decreasing max_i |A_ii - 1| (half
+// octaves), written to *order (inside the caller's scratch of
+// difficulty_scratch_bytes(cells) bytes).
+size_t difficulty_scratch_bytes(int cells);
 cudaError_t launch_difficulty_order(const double *A, int cells, int n, int nnz,
-                                    const int *row_ptr, const int *diag,
-                                    float *keys, int *order, cudaStream_t st);
+                                    const int *diag, void *scratch, int **order,
+                                    cudaStream_t st);
 
 constexpr int kMaxE = 16;  // rows per lane supported by the warp kernel
 

@@ -1,91 +1,102 @@
 // Difficulty ordering of the cells for the warp-packed solve.  The cells that
 // share a warp run in lockstep until the last one converges, so pairing cells
 // of similar iteration counts wastes fewer lanes, and solving the hardest
-// first shortens the tail.  The estimate is the largest Jacobi-scaled
-// off-diagonal row sum, max_i sum_{j != i} |A_ij| / |A_ii|, formed in FP32
-// (the FP64 pipe is left to the solve); cells are then bucketed on log2 of it
-// by one thread block (order inside a bucket is arbitrary: a cell's result
-// does not depend on where it is solved).
+// first shortens the end of the launch (the last groups are the short ones).
+// The estimate is the largest departure of a diagonal entry from one,
+// max_i |A_ii - 1|: for the step matrix I - gamma J it is gamma times the
+// largest loss rate, the stiffness of the cell's step.  Only the diagonal is
+// read (the sectors it touches stay in L2 for the solve).  Cells are binned
+// on half octaves of the estimate (hardest bin first) by a counting sort:
+// one launch classifies and counts, one scatters; the order inside a bin is
+// arbitrary, since a cell's result does not depend on where it is solved.
 #include "warp_common.cuh"
 
 namespace camp {
-
 namespace {
 
-constexpr int kBuckets = 1024;
+constexpr int kClasses = 64;
+// class of an estimate from its high word: half-octave index (exponent and
+// first fraction bit), largest first; estimates >= 12 share class 0, those
+// below 2^-29 (and zero) class kClasses - 1
+__device__ __forceinline__ int class_of(unsigned hi) {
+  const int idx = (int)(hi >> 19);            // 2 * exponent + top fraction bit
+  const int top = ((1023 + 3) << 1) | 1;
+  const int c = top - idx;
+  return c < 0 ? 0 : (c >= kClasses ? kClasses - 1 : c);
+}
 
-__global__ void difficulty_kernel(const double *__restrict__ A, int cells, int n,
-                                  int nnz, const int *__restrict__ rp,
-                                  const int *__restrict__ diag,
-                                  float *__restrict__ keys) {
+__global__ void classify_kernel(const double *__restrict__ A, int cells, int n, int nnz,
+                                const int *__restrict__ diag, unsigned char *__restrict__ cls,
+                                int *__restrict__ counts) {
   const int lane = threadIdx.x & 31;
   const int warps = (gridDim.x * blockDim.x) >> 5;
   for (int c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; c < cells; c += warps) {
     const double *Ac = A + (size_t)c * nnz;
-    float worst = 0.0f;
+    unsigned worst = 0;  // high word of max |A_ii - 1| (non-negative: ordered as integers)
     for (int i = lane; i < n; i += 32) {
-      const int d = __ldg(diag + i);
-      float off = 0.0f;
-      for (int k = __ldg(rp + i); k < __ldg(rp + i + 1); ++k)
-        if (k != d) off += fabsf(d2f_rn(__ldg(Ac + k)));
-      const float dd = fabsf(d2f_rn(__ldg(Ac + d)));
-      const float ratio = dd > 0.0f ? off / dd : 3.0e38f;
-      worst = fmaxf(worst, ratio);
+      const double d = fabs(__ldg(Ac + __ldg(diag + i)) - 1.0);
+      const unsigned hi = (unsigned)((unsigned long long)__double_as_longlong(d) >> 32);
+      worst = hi > worst ? hi : worst;
     }
+    worst = __reduce_max_sync(kFull, worst);
+    if (lane == 0) {
+      const int k = class_of(worst);
+      cls[c] = (unsigned char)k;
+      atomicAdd(counts + k, 1);
+    }
+  }
+}
+
+// counts[0..kClasses) per-class totals, counts[kClasses..) running cursors
+__global__ void scatter_kernel(const unsigned char *__restrict__ cls, int cells,
+                               int *__restrict__ counts, int *__restrict__ order) {
+  __shared__ int start[kClasses];
+  if (threadIdx.x < 32) {
+    // exclusive prefix of the class totals, two classes per lane
+    const int l = threadIdx.x;
+    const int a = counts[2 * l], b = counts[2 * l + 1];
+    int s = a + b;
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) worst = fmaxf(worst, __shfl_xor_sync(kFull, worst, o));
-    if (lane == 0) keys[c] = worst;
+    for (int o = 1; o < 32; o <<= 1) {
+      const int t = __shfl_up_sync(kFull, s, o);
+      if (l >= o) s += t;
+    }
+    start[2 * l] = s - a - b;
+    start[2 * l + 1] = s - b;
   }
-}
-
-__device__ __forceinline__ int bucket_of(float key) {
-  // decreasing difficulty: larger keys get smaller bucket indices
-  const float l = key > 0.0f ? __log2f(key) : -1000.0f;
-  int b = (int)floorf(l * 32.0f) + 800;
-  b = b < 0 ? 0 : (b >= kBuckets ? kBuckets - 1 : b);
-  return kBuckets - 1 - b;
-}
-
-__global__ void __launch_bounds__(kBuckets) order_kernel(const float *__restrict__ keys,
-                                                         int cells, int *__restrict__ order) {
-  __shared__ int hist[kBuckets];
-  __shared__ int scan[kBuckets];
-  const int t = threadIdx.x;
-  hist[t] = 0;
   __syncthreads();
-  for (int c = t; c < cells; c += blockDim.x) atomicAdd(&hist[bucket_of(keys[c])], 1);
-  __syncthreads();
-  // exclusive scan (Hillis-Steele on the inclusive sums, then shift)
-  scan[t] = hist[t];
-  __syncthreads();
-  for (int off = 1; off < kBuckets; off <<= 1) {
-    const int v = t >= off ? scan[t - off] : 0;
-    __syncthreads();
-    scan[t] += v;
-    __syncthreads();
-  }
-  hist[t] = scan[t] - hist[t];   // start of bucket t
-  __syncthreads();
-  for (int c = t; c < cells; c += blockDim.x) {
-    const int p = atomicAdd(&hist[bucket_of(keys[c])], 1);
-    order[p] = c;
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c < cells) {
+    const int k = cls[c];
+    order[start[k] + atomicAdd(counts + kClasses + k, 1)] = c;
   }
 }
 
 }  // namespace
 
+size_t difficulty_scratch_bytes(int cells) {
+  // class bytes (rounded to 16), the order, the class totals and cursors
+  return (((size_t)cells + 15) & ~(size_t)15) + (size_t)cells * sizeof(int) +
+         2 * kClasses * sizeof(int);
+}
+
 cudaError_t launch_difficulty_order(const double *A, int cells, int n, int nnz,
-                                    const int *row_ptr, const int *diag,
-                                    float *keys, int *order, cudaStream_t st) {
+                                    const int *diag, void *scratch, int **order,
+                                    cudaStream_t st) {
+  unsigned char *cls = (unsigned char *)scratch;
+  int *ord = (int *)(cls + (((size_t)cells + 15) & ~(size_t)15));
+  int *counts = ord + cells;
+  *order = ord;
   if (cells <= 0) return cudaSuccess;
+  cudaError_t e = cudaMemsetAsync(counts, 0, 2 * kClasses * sizeof(int), st);
+  if (e != cudaSuccess) return e;
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  const int warps_needed = cells;
-  int blocks = (warps_needed * 32 + 255) / 256;
+  int blocks = (cells * 32 + 255) / 256;
   if (blocks > sms * 8) blocks = sms * 8;
-  difficulty_kernel<<<blocks, 256, 0, st>>>(A, cells, n, nnz, row_ptr, diag, keys);
-  order_kernel<<<1, kBuckets, 0, st>>>(keys, cells, order);
+  classify_kernel<<<blocks, 256, 0, st>>>(A, cells, n, nnz, diag, cls, counts);
+  scatter_kernel<<<(cells + 255) / 256, 256, 0, st>>>(cls, cells, counts, ord);
   return cudaGetLastError();
 }
 

@@ -297,9 +297,8 @@ struct camp_solver {
   Mechanism mech;
   // difficulty ordering (camp_solver_set_ordering): scratch grown on demand
   int ordering = 0;
-  float *d_keys = nullptr;
-  int *d_order = nullptr;
-  size_t order_cap = 0;
+  void *d_order_scratch = nullptr;
+  size_t order_cap = 0;  // bytes
 };
 
 namespace {
@@ -450,25 +449,21 @@ camp_status do_solve(camp_solver_t h, int cells, const double *A_vals,
     a.queue = h->d_queue + 2 * queue_slot;
     a.order = nullptr;
     if (h->ordering && cells > 1 && queue_slot == 0) {
-      if ((size_t)cells > h->order_cap) {
-        cudaFree(h->d_keys);
-        cudaFree(h->d_order);
-        h->d_keys = nullptr;
-        h->d_order = nullptr;
+      const size_t need = difficulty_scratch_bytes(cells);
+      if (need > h->order_cap) {
+        cudaFree(h->d_order_scratch);
+        h->d_order_scratch = nullptr;
         h->order_cap = 0;
-        if ((e = cudaMalloc(&h->d_keys, (size_t)cells * sizeof(float))) != cudaSuccess ||
-            (e = cudaMalloc(&h->d_order, (size_t)cells * sizeof(int))) != cudaSuccess)
+        if ((e = cudaMalloc(&h->d_order_scratch, need)) != cudaSuccess)
           return fail(CAMP_ENOMEM, "ordering scratch: %s", cudaGetErrorString(e));
-        h->order_cap = (size_t)cells;
+        h->order_cap = need;
       }
-      if (flags & CAMP_TRANSPOSE)
-        e = launch_difficulty_order(A_vals, cells, h->tr.n, h->tr.nnz, h->fwd.d_rp,
-                                    h->fwd.d_diag, h->d_keys, h->d_order, st);
-      else
-        e = launch_difficulty_order(A_vals, cells, v.n, v.nnz, v.d_rp, v.d_diag,
-                                    h->d_keys, h->d_order, st);
+      // the diagonal is the same in both orientations: forward positions
+      int *order = nullptr;
+      e = launch_difficulty_order(A_vals, cells, h->fwd.n, h->fwd.nnz, h->fwd.d_diag,
+                                  h->d_order_scratch, &order, st);
       if (e != cudaSuccess) return cuda_fail(e, "difficulty ordering");
-      a.order = h->d_order;
+      a.order = order;
     }
     int occ = 0;
     e = warp_occupancy(E, wpb, smem, &occ);
@@ -627,8 +622,7 @@ camp_status camp_solver_destroy(camp_solver_t h) {
   for (auto &kv : h->mech.by_lanes) kv.second.release();
   cudaFree(h->d_row_of);
   cudaFree(h->d_queue);
-  cudaFree(h->d_keys);
-  cudaFree(h->d_order);
+  cudaFree(h->d_order_scratch);
   cudaFree(h->h_dA); cudaFree(h->h_db); cudaFree(h->h_dx);
   cudaFree(h->h_dres); cudaFree(h->h_dit); cudaFree(h->h_dst);
   for (auto &s : h->h_streams) if (s) cudaStreamDestroy(s);
