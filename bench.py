@@ -115,7 +115,7 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def cpu_baseline(mech, A, b, tol, maxit, min_seconds=10.0):
+def cpu_baseline(mech, A, b, tol, maxit, min_seconds=10.0, single_seconds=3.0):
     import oracle
     threads = os.cpu_count() or 1
     done, t0 = 0, time.perf_counter()
@@ -127,9 +127,19 @@ def cpu_baseline(mech, A, b, tol, maxit, min_seconds=10.0):
         el = time.perf_counter() - t0
         if el >= min_seconds:
             break
+    # one core, on leading slices of the same cells
+    one, t1, chunk = 0, time.perf_counter(), min(A.shape[0], 1000)
+    while True:
+        oracle.solve(mech.row_ptr, mech.col_idx, A[:chunk], b[:chunk], tol, maxit, threads=1)
+        one += chunk
+        el1 = time.perf_counter() - t1
+        if el1 >= single_seconds:
+            break
     return {"value": done / el, "unit": UNIT, "cores": int(used), "kind": "oracle",
             "sample": f"the full {A.shape[0]}-cell workload solved {done // A.shape[0]}x "
-                      f"({el:.1f} s, {used} threads, plain C FP64)"}
+                      f"({el:.1f} s, {used} threads, plain C FP64)",
+            "value_1core": one / el1,
+            "sample_1core": f"the first {chunk} cells solved {one // chunk}x ({el1:.1f} s, 1 thread)"}
 
 
 def run_reference(args, rank, world):
@@ -270,6 +280,33 @@ def time_uneven(camp, dev, flush, stream, steps=50):
             "persistent_graph": {"ms_per_step": mb, "value": cells / (mb * 1e-3), "unit": UNIT},
             "three_plain_launches": {"ms_per_step": mp, "value": cells / (mp * 1e-3), "unit": UNIT},
             "converged": conv, "iters_mean": float(iters.mean()), "iters_max": int(iters.max())}
+
+
+def fp64_rate(camp, dev):
+    """Measured FP64 FMA rate of this GPU (GFLOP/s, 2 flops per FMA): the
+    library's probe of independent dependent-FMA chains, 64 warps per SM on
+    every SM, timed with CUDA events (median of 5)."""
+    import ctypes
+    import torch
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    n, steps = sms * 2048, 4096
+    x = torch.rand(n, dtype=torch.float64, device=dev)
+    y = torch.empty_like(x)
+    f = camp._lib.camp_selftest
+    f.restype = ctypes.c_int
+    f.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
+                  ctypes.c_void_p]
+    s = torch.cuda.current_stream(dev)
+    ts = []
+    for _ in range(6):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(s)
+        assert f(6, n, x.data_ptr(), y.data_ptr(), steps, s.cuda_stream) == 0
+        e1.record(s)
+        torch.cuda.synchronize(dev)
+        ts.append(e0.elapsed_time(e1))
+    ms = sorted(ts[1:])[2]
+    return 2.0 * 4 * n * steps / (ms * 1e-3) / 1e9
 
 
 def time_fused(camp, cb, tol, maxit, flush, stream, dev, steps=200):
@@ -535,6 +572,7 @@ def main():
     uneven = None
     fused = None
     newton = None
+    fp64_measured = None
     if not args.skip_extras:
         if args.mode == "fp64":
             mt = time_steps(solve_mixed, flush, stream, 200, 5)
@@ -548,6 +586,7 @@ def main():
                 "converged": int((st == 0).sum().item()),
                 "speedup_vs_fp64": ms_step / mms}
         e2e = time_e2e(camp, solver, cb, C, tol, maxit, args.e2e_steps, world, dev)
+        fp64_measured = fp64_rate(camp, dev)
         fused = time_fused(camp, cb, tol, maxit, flush, stream, dev)
         newton = time_newton(camp, cb, flush, stream, dev)
         uneven = time_uneven(camp, dev, flush, stream) if rank == 0 else None
@@ -583,6 +622,10 @@ def main():
         if args.mode == "mixed":
             line["config"]["sweeps_mean"] = float(sw.mean())
             line["roofline"] = None
+        if fp64_measured is not None and line["roofline"] is not None:
+            # the same achieved rate against the FMA rate measured on this GPU
+            line["roofline"]["peak_measured"] = fp64_measured
+            line["roofline"]["frac_of_measured"] = line["roofline"]["achieved"] / fp64_measured
         if mixed_side is not None:
             line["mixed_fp32_inner"] = mixed_side
         if uneven is not None:

@@ -16,7 +16,10 @@
  *         once);
  *   op 4: the same sum by the FP64 shuffle tree;
  *   op 5: the op-3 sum with its reductions done by full-warp redux.sync
- *         (bit-identical to op 3 by construction).
+ *         (bit-identical to op 3 by construction);
+ *   op 6: FP64 rate probe: each of n threads runs four independent chains
+ *         of `lanes` dependent FMAs from in[i] and writes their sum to
+ *         out[i] (4 * n * lanes DFMAs to time; lanes in [1, 2^20]).
  * For ops 3 to 5, n must be a multiple of 32 and lanes a power of two in
  * [1, 32].  Returns CAMP_EINVAL for bad arguments, CAMP_ECUDA if the launch
  * fails.  The paper has no counterpart: this is test support.

@@ -87,3 +87,16 @@ def test_integer_segment_sum_is_exact_to_one_rounding(cuda, lanes):
         seg = x[s:s + lanes]
         exact = math.fsum(seg)
         assert abs(tree[s] - exact) <= levels * 2.0 ** -53 * np.abs(seg).sum() * 1.0001 + 1e-300
+
+
+def test_fp64_rate_probe_computes_its_chains(cuda):
+    """op 6 (the FP64 rate probe timed by bench.py) runs four chains
+    a <- a*m + q per thread; its output matches the chains' closed form."""
+    steps = 1000
+    x = np.random.default_rng(6).random(32 * 64)
+    y = _run(6, x, steps)
+    m, q = 0.999999999, 1e-9
+    ms = m ** steps
+    chain = lambda a0: ms * a0 + q * (1 - ms) / (1 - m)
+    expect = chain(x) + chain(x + 1) + chain(x + 2) + chain(x + 3)
+    np.testing.assert_allclose(y, expect, rtol=1e-12)
