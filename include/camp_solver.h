@@ -169,12 +169,16 @@ camp_status camp_solver_grad_A(camp_solver_t h, int cells,
                                double *gA);
 
 /*
- * End-to-end solve from HOST memory: copies A_vals and b to the device in
- * chunks, solves each chunk while the next one is copied, and copies x,
- * iters and resid back; returns after everything is back in host memory.
- * Host arrays should be page-locked for full speed (pageable memory works but
- * the copies are synchronous).  status_out may be NULL.  Device staging
- * buffers are owned by the handle and grow on demand.
+ * End-to-end solve from HOST memory: copies b and then A_vals to the device
+ * (A in chunks of shrinking size), solves each chunk while the next one is
+ * copied, and returns after every result is in host memory.  When x,
+ * iters_out, resid_out (and status_out) are device-addressable host memory
+ * (page-locked/mapped), the kernels write them in place; otherwise results
+ * are staged on the device and copied back per chunk.  Host arrays should be
+ * page-locked for full speed (pageable memory works but the copies are
+ * synchronous).  status_out may be NULL.  Device staging buffers are owned by
+ * the handle and grow on demand.  The call synchronizes with its own copy
+ * and solve streams only.
  */
 camp_status camp_solver_solve_host(camp_solver_t h, int cells,
                                    const double *A_vals, const double *b,

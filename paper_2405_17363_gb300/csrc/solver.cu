@@ -50,7 +50,7 @@ cudaError_t launch_warp(int E, const WarpArgs &a, int wpb, int grid,
     default: return cudaErrorInvalidValue;
   }
 }
-cudaError_t warp_occupancy(int E, int wpb, size_t smem, int *blocks) {
+static cudaError_t warp_occupancy_query(int E, int wpb, size_t smem, int *blocks) {
   switch (E) {
 #define C(E) case E: return occ_warp_##E(wpb, smem, blocks);
     C(1) C(2) C(3) C(4) C(5) C(6) C(7) C(8) C(9) C(10) C(11) C(12) C(13)
@@ -58,6 +58,30 @@ cudaError_t warp_occupancy(int E, int wpb, size_t smem, int *blocks) {
 #undef C
     default: return cudaErrorInvalidValue;
   }
+}
+
+// The occupancy of a launch shape does not change: remember the answers
+// (fixed-size record, no heap allocation).
+cudaError_t warp_occupancy(int E, int wpb, size_t smem, int *blocks) {
+  struct Entry { int dev, E, wpb; size_t smem; int blocks; };
+  static std::mutex mu;
+  static Entry memo[256];
+  static int nmemo = 0;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  {
+    std::lock_guard<std::mutex> lock(mu);
+    for (int i = 0; i < nmemo; ++i)
+      if (memo[i].dev == dev && memo[i].E == E && memo[i].wpb == wpb && memo[i].smem == smem) {
+        *blocks = memo[i].blocks;
+        return cudaSuccess;
+      }
+  }
+  if ((e = warp_occupancy_query(E, wpb, smem, blocks)) != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lock(mu);
+  if (nmemo < 256) memo[nmemo++] = Entry{dev, E, wpb, smem, *blocks};
+  return cudaSuccess;
 }
 
 cudaError_t launch_mixed(int E, const MixedArgs &a, int wpb, int grid,
@@ -116,7 +140,7 @@ CAMP_OCCUPANCY8(newton_occupancy, newton)
 #undef CAMP_DISPATCH8
 #undef CAMP_OCCUPANCY8
 
-constexpr int kHostChunks = 8;        // pipeline depth of camp_solver_solve_host
+constexpr int kHostChunks = 6;        // pipeline depth of camp_solver_solve_host
 constexpr int kHostSolveStreams = 4;  // concurrent chunk solves
 
 cudaError_t ensure_max_smem(const void *kernel) {
@@ -292,7 +316,7 @@ struct camp_solver {
   // copies, [2 ..] solves (round robin, so the solves of consecutive chunks
   // overlap); per chunk an event after its input copy and one after its solve
   cudaStream_t h_streams[2 + kHostSolveStreams] = {};
-  cudaEvent_t h_in[kHostChunks] = {}, h_done[kHostChunks] = {};
+  cudaEvent_t h_in[kHostChunks] = {}, h_done[kHostChunks] = {}, h_start = nullptr;
   std::mutex mu;
   Mechanism mech;
   // difficulty ordering (camp_solver_set_ordering): scratch grown on demand
@@ -628,6 +652,7 @@ camp_status camp_solver_destroy(camp_solver_t h) {
   for (auto &s : h->h_streams) if (s) cudaStreamDestroy(s);
   for (auto &ev : h->h_in) if (ev) cudaEventDestroy(ev);
   for (auto &ev : h->h_done) if (ev) cudaEventDestroy(ev);
+  if (h->h_start) cudaEventDestroy(h->h_start);
   delete h;
   return CAMP_OK;
 }
@@ -752,36 +777,67 @@ camp_status camp_solver_solve_host(camp_solver_t h, int cells,
       return cuda_fail(e, "event create");
   cudaStream_t sin = h->h_streams[0], sout = h->h_streams[1];
   // order after earlier work on the handle's stream
-  cudaEvent_t ev0;
-  if ((e = cudaEventCreateWithFlags(&ev0, cudaEventDisableTiming)) != cudaSuccess)
+  if (!h->h_start && (e = cudaEventCreateWithFlags(&h->h_start, cudaEventDisableTiming)) != cudaSuccess)
     return cuda_fail(e, "event create");
-  cudaEventRecord(ev0, h->stream);
-  for (int q = 0; q < 2 + kHostSolveStreams; ++q) cudaStreamWaitEvent(h->h_streams[q], ev0, 0);
-  cudaEventDestroy(ev0);
-  // pipeline: every chunk's input is copied back to back on the copy-in
-  // stream (the host link stays busy), its solve starts on the next solve
-  // stream once that copy has landed (solves of consecutive chunks overlap, so
-  // a chunk's tail does not idle the GPU), its results go back on the
-  // copy-out stream once the solve is done
-  const int nchunk = cells >= kHostChunks * 512 ? kHostChunks : 1;
-  const int per = (cells + nchunk - 1) / nchunk;
-  camp_status rs = CAMP_OK;
+  cudaEventRecord(h->h_start, h->stream);
+  for (int q = 0; q < 2 + kHostSolveStreams; ++q) cudaStreamWaitEvent(h->h_streams[q], h->h_start, 0);
+  // Outputs in host memory the device can address (pinned or mapped) are
+  // written by the kernels directly; otherwise they are staged on the device
+  // and copied back per chunk.
+  auto device_view = [](const void *p) -> void * {
+    cudaPointerAttributes pa;
+    if (cudaPointerGetAttributes(&pa, p) != cudaSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
+    return (pa.type == cudaMemoryTypeHost || pa.type == cudaMemoryTypeManaged) ? pa.devicePointer
+                                                                               : nullptr;
+  };
+  double *dx = (double *)device_view(x);
+  int *dit = (int *)device_view(iters_out);
+  double *dres = (double *)device_view(resid_out);
+  int *dst = status_out ? (int *)device_view(status_out) : nullptr;
+  const bool direct = dx && dit && dres && (!status_out || dst);
+  // Pipeline: b in one copy, then A in chunks of shrinking size back to back
+  // on the copy-in stream (few large copies keep the host link busy; a small
+  // last chunk keeps the solve after the last byte short); each chunk's solve
+  // starts on the next solve stream once its A has landed, so the solves of
+  // consecutive chunks overlap.
+  int nchunk = 1;
+  while (nchunk < kHostChunks && cells >= (nchunk + 1) * 1024) ++nchunk;
+  int c0s[kHostChunks + 1];
+  {
+    long tw = 0, acc = 0;
+    for (int q = 0; q < nchunk; ++q) tw += nchunk + 2 - q;
+    c0s[0] = 0;
+    for (int q = 0; q < nchunk; ++q) {
+      acc += nchunk + 2 - q;
+      c0s[q + 1] = (int)((long)cells * acc / tw);
+    }
+    c0s[nchunk] = cells;
+  }
+  cudaMemcpyAsync(h->h_db, b, (size_t)cells * n * 8, cudaMemcpyHostToDevice, sin);
   for (int q = 0; q < nchunk; ++q) {
-    const int c0 = q * per;
-    const int cn = std::min(per, cells - c0);
-    if (cn <= 0) break;
+    const int c0 = c0s[q], cn = c0s[q + 1] - c0;
     cudaMemcpyAsync(h->h_dA + (size_t)c0 * nnz, A_vals + (size_t)c0 * nnz,
                     (size_t)cn * nnz * 8, cudaMemcpyHostToDevice, sin);
-    cudaMemcpyAsync(h->h_db + (size_t)c0 * n, b + (size_t)c0 * n,
-                    (size_t)cn * n * 8, cudaMemcpyHostToDevice, sin);
     cudaEventRecord(h->h_in[q], sin);
   }
+  camp_status rs = CAMP_OK;
   for (int q = 0; q < nchunk; ++q) {
-    const int c0 = q * per;
-    const int cn = std::min(per, cells - c0);
-    if (cn <= 0) break;
+    const int c0 = c0s[q], cn = c0s[q + 1] - c0;
+    if (cn <= 0) continue;
     cudaStream_t scomp = h->h_streams[2 + q % kHostSolveStreams];
     cudaStreamWaitEvent(scomp, h->h_in[q], 0);
+    if (direct) {
+      rs = do_solve(h, cn, h->h_dA + (size_t)c0 * nnz, h->h_db + (size_t)c0 * n,
+                    dx + (size_t)c0 * n, tol, maxit, dit + c0, dres + c0,
+                    dst ? dst + c0 : nullptr, 0, scomp, 1 + q % kHostSolveStreams);
+      if (rs != CAMP_OK) break;
+      cudaEventRecord(h->h_done[q], scomp);
+      cudaStreamWaitEvent(sout, h->h_done[q], 0);
+      continue;
+    }
     rs = do_solve(h, cn, h->h_dA + (size_t)c0 * nnz, h->h_db + (size_t)c0 * n,
                   h->h_dx + (size_t)c0 * n, tol, maxit, h->h_dit + c0,
                   h->h_dres + c0, h->h_dst + c0, 0, scomp, 1 + q % kHostSolveStreams);
@@ -798,12 +854,13 @@ camp_status camp_solver_solve_host(camp_solver_t h, int cells,
       cudaMemcpyAsync(status_out + c0, h->h_dst + c0, (size_t)cn * 4,
                       cudaMemcpyDeviceToHost, sout);
   }
-  cudaError_t es = cudaSuccess;
-  for (int q = 0; q < 2 + kHostSolveStreams; ++q) {
-    const cudaError_t eq = cudaStreamSynchronize(h->h_streams[q]);
-    if (es == cudaSuccess) es = eq;
+  // every stream's work precedes the copy-out stream's last wait or copy
+  cudaError_t es = rs == CAMP_OK ? cudaStreamSynchronize(sout) : cudaSuccess;
+  if (rs != CAMP_OK) {
+    for (int q = 0; q < 2 + kHostSolveStreams; ++q) cudaStreamSynchronize(h->h_streams[q]);
+    return rs;
   }
-  if (rs != CAMP_OK) return rs;
+  if (es == cudaSuccess) es = cudaGetLastError();
   if (es != cudaSuccess) return cuda_fail(es, "solve_host");
   return CAMP_OK;
 }

@@ -69,10 +69,15 @@ def test_grad_kernel_exact(cuda):
     s.close()
 
 
-def test_solve_host_equals_device(cuda):
+@pytest.mark.parametrize("cells,pinned_out", [(5000, True), (10000, True), (700, True),
+                                              (5000, False)])
+def test_solve_host_equals_device(cuda, cells, pinned_out):
+    """The host-memory entry point (chunked copies, outputs written in place
+    when the host arrays are device-addressable, staged and copied back
+    otherwise) gives the device solve's bits."""
     import torch
     from paper_2405_17363_gb300 import camp
-    cbs, tol, maxit = synth.workload(1, cells=5000)
+    cbs, tol, maxit = synth.workload(1, cells=cells)
     cb = cbs[0]
     m = cb.mech
     s = camp.Solver(m.row_ptr, m.col_idx)
@@ -82,10 +87,11 @@ def test_solve_host_equals_device(cuda):
     C = cb.cells
     hA = torch.as_tensor(cb.A_vals).pin_memory()
     hb = torch.as_tensor(cb.b).pin_memory()
-    hx = torch.empty((C, m.n), dtype=torch.float64).pin_memory()
-    hit = torch.empty(C, dtype=torch.int32).pin_memory()
-    hr = torch.empty(C, dtype=torch.float64).pin_memory()
-    hs = torch.empty(C, dtype=torch.int32).pin_memory()
+    pin = (lambda t: t.pin_memory()) if pinned_out else (lambda t: t)
+    hx = pin(torch.full((C, m.n), np.nan, dtype=torch.float64))
+    hit = pin(torch.full((C,), -7, dtype=torch.int32))
+    hr = pin(torch.full((C,), np.nan, dtype=torch.float64))
+    hs = pin(torch.full((C,), -7, dtype=torch.int32))
     camp.camp_solver_solve_host(s.h, C, hA, hb, hx, tol, maxit, hit, hr, hs)
     np.testing.assert_array_equal(hx.numpy(), xd.cpu().numpy())
     np.testing.assert_array_equal(hit.numpy(), itd.cpu().numpy())
