@@ -13,8 +13,8 @@
 
 namespace camp {
 
-template <int E>
-__global__ void __launch_bounds__(256, 2) mixed_refine_kernel(const MixedArgs a) {
+template <int E, int LC>
+__device__ __forceinline__ void mixed_body(const MixedArgs &a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   SchedWord *sch_s = reinterpret_cast<SchedWord *>(smem_raw);
   const int nsch = a.L * a.Lc;
@@ -22,9 +22,10 @@ __global__ void __launch_bounds__(256, 2) mixed_refine_kernel(const MixedArgs a)
 
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
-  const int seg = lane >> a.log2Lc;
-  const int sl = lane & (a.Lc - 1);
-  const int Lc = a.Lc, n = a.n, nnz = a.nnz;
+  const int Lc = LC ? LC : a.Lc;  // lanes per cell (compile-time when LC > 0)
+  const int seg = LC ? lane / LC : lane >> a.log2Lc;
+  const int sl = lane & (Lc - 1);
+  const int n = a.n, nnz = a.nnz;
   // bytes per cell: 12 segA + 16 segV + 12 segV (FP64 A, FP32 A, 2 FP64 + 3 FP32 vectors)
   const size_t cellBytes = (size_t)12 * a.segA + (size_t)28 * a.segV;
   unsigned char *wb = smem_raw + sched_smem_bytes(nsch) +
@@ -44,7 +45,7 @@ __global__ void __launch_bounds__(256, 2) mixed_refine_kernel(const MixedArgs a)
   const int warps_total = gridDim.x * (blockDim.x >> 5);
 
   for (int g = blockIdx.x * (blockDim.x >> 5) + warp; g < a.ngroups; g += warps_total) {
-    const int c = g * a.k + seg;
+    const int c = g * (LC ? 32 / LC : a.k) + seg;
     const bool has = c < a.cells;
     {  // stage A in slot order, FP64 and its FP32 rounding
       const double *Ac = a.A + (size_t)(has ? c : 0) * nnz;
@@ -71,7 +72,7 @@ __global__ void __launch_bounds__(256, 2) mixed_refine_kernel(const MixedArgs a)
         xv[e] = 0.0;
         acc[0] = fma(bi, bi, acc[0]);
       }
-      bb = seg_sum_exact(acc[0], Lc);
+      bb = seg_sum_x<LC>(acc[0], Lc);
     }
     const double thr = (a.tol * a.tol) * bb;  // (tol ||b||)^2
     int st = -1, sweeps = 0, inner = 0;
@@ -103,7 +104,7 @@ __global__ void __launch_bounds__(256, 2) mixed_refine_kernel(const MixedArgs a)
         r[e] = pass > 0 ? bi - o64[i] : bi;
         rr[0] = fma(r[e], r[e], rr[0]);
       }
-      rr[0] = seg_sum_exact(rr[0], Lc);
+      rr[0] = seg_sum_x<LC>(rr[0], Lc);
       if (!done) {
         // ||r|| <= tol ||b|| on the bit patterns; the relative residual itself
         // (a square root and a division) is formed once, at the end
@@ -250,6 +251,18 @@ __global__ void __launch_bounds__(256, 2) mixed_refine_kernel(const MixedArgs a)
     }
     __syncwarp();
   }
+}
+
+template <int E>
+__global__ void __launch_bounds__(256, 2) mixed_refine_kernel(const MixedArgs a) {
+  // the automatic choice (at most 3 rows per lane on 8, 16 or 32 lanes) runs
+  // code with the lane count fixed at compile time
+  if constexpr (E >= 2 && E <= 3) {
+    if (a.Lc == 32) return mixed_body<E, 32>(a);
+    if (a.Lc == 16) return mixed_body<E, 16>(a);
+    if (a.Lc == 8) return mixed_body<E, 8>(a);
+  }
+  mixed_body<E, 0>(a);
 }
 
 }  // namespace camp

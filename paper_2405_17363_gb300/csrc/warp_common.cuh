@@ -390,4 +390,14 @@ __device__ __forceinline__ double seg_sum_exact_redux(double v) {
   return __longlong_as_double((long long)out);
 }
 
+// Exact segment sum.  With Lc known at compile time (LC > 0) and at most two
+// cells per warp, the reductions run as full-warp redux.sync (one instruction
+// each; a redux over part of a warp measured several times slower than
+// shuffles); otherwise the shuffle form.  Both give the same bits.
+template <int LC>
+__device__ __forceinline__ double seg_sum_x(double v, int Lc) {
+  if constexpr (LC >= 16) return seg_sum_exact_redux<32 / LC>(v);
+  else return seg_sum_exact(v, Lc);
+}
+
 }  // namespace camp

@@ -31,17 +31,9 @@ namespace camp {
 #define CAMP_EXACT_SUMS 1  // segment sums on the integer pipe (0: FP64 shuffle tree)
 #endif
 
-// Exact segment sum.  With Lc known at compile time and at most two cells
-// per warp, the reductions run as full-warp redux.sync (one instruction each;
-// a redux over part of a warp measured several times slower than shuffles).
-template <int LC>
-__device__ __forceinline__ double xsum(double v, int Lc) {
-  if constexpr (LC >= 16) return seg_sum_exact_redux<32 / LC>(v);
-  else return seg_sum_exact(v, Lc);
-}
 template <int LC>
 __device__ __forceinline__ double ssum1(double v, int Lc) {
-  if (CAMP_EXACT_SUMS) return xsum<LC>(v, Lc);
+  if (CAMP_EXACT_SUMS) return seg_sum_x<LC>(v, Lc);
   double a[1] = {v};
   seg_sum<1>(a, Lc);
   return a[0];
@@ -49,8 +41,8 @@ __device__ __forceinline__ double ssum1(double v, int Lc) {
 template <int LC>
 __device__ __forceinline__ void ssum2(double &a, double &b, int Lc) {
   if (CAMP_EXACT_SUMS) {
-    a = xsum<LC>(a, Lc);
-    b = xsum<LC>(b, Lc);
+    a = seg_sum_x<LC>(a, Lc);
+    b = seg_sum_x<LC>(b, Lc);
   } else {
     seg_sum2(a, b, Lc);
   }
@@ -58,9 +50,9 @@ __device__ __forceinline__ void ssum2(double &a, double &b, int Lc) {
 template <int LC>
 __device__ __forceinline__ void ssum3(double &a, double &b, double &c, int Lc) {
   if (CAMP_EXACT_SUMS) {
-    a = xsum<LC>(a, Lc);
-    b = xsum<LC>(b, Lc);
-    c = xsum<LC>(c, Lc);
+    a = seg_sum_x<LC>(a, Lc);
+    b = seg_sum_x<LC>(b, Lc);
+    c = seg_sum_x<LC>(c, Lc);
   } else {
     seg_sum3(a, b, c, Lc);
   }
