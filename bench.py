@@ -40,7 +40,7 @@ FP64_PEAK_GFLOPS = 4 * 152 * 2.07
 # DRAM bytes (read + write) per launch of the headline kernel from one ncu
 # capture (dram__bytes_read.sum + dram__bytes_write.sum), valid only for the
 # library revision it was taken on; any other revision reports null.
-TRAFFIC_BYTES = {"campsolve 0.9 (sm_103a)": 51.684e6}
+TRAFFIC_BYTES = {"campsolve 0.10 (sm_103a)": 51.665e6}
 
 
 def peaks():
