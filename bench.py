@@ -365,6 +365,22 @@ def time_newton(camp, cb, flush, stream, dev, steps=50, newton_tol=1e-10, lin_to
     return res
 
 
+def run_step_case(args):
+    """--case fused / --case newton: the in-kernel assembly + solve, or the
+    device Newton corrector, alone on the 80-species cells (for profiling)."""
+    import torch
+    from paper_2405_17363_gb300 import camp
+    dev = torch.device("cuda", 0)
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+    cbs, tol, maxit = synth.workload(WORKLOAD_ID)
+    st = torch.cuda.current_stream()
+    if args.case == "fused":
+        res = time_fused(camp, cbs[0], tol, maxit, flush, st, dev, steps=args.steps)
+    else:
+        res = time_newton(camp, cbs[0], flush, st, dev, steps=args.steps)
+    print(json.dumps({"case": args.case, **res}), flush=True)
+
+
 def run_uneven_case(args):
     """--case uneven: the persistent batch alone, timed as the step."""
     import torch
@@ -492,9 +508,12 @@ def main():
     ap.add_argument("--mode", default="fp64", choices=["fp64", "mixed"],
                     help="fp64: plain FP64 solve (the headline); mixed: FP32-inner refinement")
     ap.add_argument("--case", default="headline",
-                    choices=["headline", "uneven", "arrangements", "variability"],
+                    choices=["headline", "uneven", "arrangements", "variability", "fused",
+                             "newton"],
                     help="headline: the 80-species 10k-cell FP64 solve; uneven: time the "
-                         "persistent multi-mechanism batch as the step (for profiling)")
+                         "persistent multi-mechanism batch as the step; fused / newton: the "
+                         "in-kernel assembly or the device Newton corrector alone (for "
+                         "profiling)")
     ap.add_argument("--skip-extras", action="store_true",
                     help="time the device solve only (no e2e, CPU baseline or mixed side run)")
     args = ap.parse_args()
@@ -513,6 +532,8 @@ def main():
         return run_arrangements_case(args)
     if args.case == "variability":
         return run_variability_case(args)
+    if args.case in ("fused", "newton"):
+        return run_step_case(args)
 
     import torch
     import torch.distributed as dist
