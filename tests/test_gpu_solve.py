@@ -200,3 +200,38 @@ def test_difficulty_ordering_gives_identical_results(camp, cuda, wid):
         for r, g in zip(ref, got):
             assert torch.equal(r, g)
     s.close()
+
+
+@pytest.mark.parametrize("n,R", [(400, 1000), (700, 1600)])
+def test_large_mechanisms(camp, cuda, n, R):
+    """Mechanisms far beyond the benchmark's: 400 species (automatic choice:
+    32 lanes, 13 rows per lane) and 700 species (beyond 16 rows per lane: the
+    automatic choice falls back to one thread per row), against the oracle."""
+    mech = synth.make_mechanism(n, R, 77 + n)
+    cb = synth.make_cells(mech, 24, 78 + n, gamma=(1e-4, 1e-1))
+    tol, maxit = 1e-10, 500
+    orc = oracle.solve(mech.row_ptr, mech.col_idx, cb.A_vals, cb.b, tol, maxit, threads=8)
+    gpu = run_gpu(camp, mech, cb.A_vals, cb.b, tol, maxit, cuda)
+    parity.compare(mech, cb.A_vals, cb.b, tol, gpu, orc, f"n={n}")
+
+
+def test_large_batch_sampled(camp, cuda):
+    """480,000 cells of 80 species in one launch (A alone is 2.2 GB, so byte
+    offsets pass 2^31): every cell converges, and 96 sampled cells, the first
+    and the last included, match the oracle."""
+    import torch
+    cbs, tol, maxit = synth.workload(1, cells=480000)
+    cb = cbs[0]
+    m = cb.mech
+    s = camp.Solver(m.row_ptr, m.col_idx)
+    x, it, res, st = s.solve(to_dev(cb.A_vals, cuda), to_dev(cb.b, cuda), tol, maxit)
+    torch.cuda.synchronize()
+    gpu = dict(x=x.cpu().numpy(), iters=it.cpu().numpy(), resid=res.cpu().numpy(),
+               status=st.cpu().numpy())
+    s.close()
+    assert np.all(gpu["status"] == 0) and np.all(gpu["resid"] <= tol)
+    idx = np.unique(np.r_[0, np.random.default_rng(48).choice(cb.cells, 94, replace=False),
+                          cb.cells - 1])
+    orc = oracle.solve(m.row_ptr, m.col_idx, cb.A_vals[idx], cb.b[idx], tol, maxit, threads=8)
+    parity.compare(m, cb.A_vals[idx], cb.b[idx], tol, {k: v[idx] for k, v in gpu.items()}, orc,
+                   "480k sampled")
