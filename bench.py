@@ -34,13 +34,15 @@ import synth  # noqa: E402
 METRIC = "solved cell-systems/s (80 species, 10k cells, 1e-10) and % of HBM roofline"
 UNIT = "cell-systems/s"
 WORKLOAD_ID = 1
+DEFAULT_ORDERING = 1  # the library default of camp_solver_set_ordering
 HBM_PEAK_FALLBACK = 6800.0
 # FP64 pipe: 2 DFMA per clock per SM (4 flops) x 152 SMs x 2.07 GHz max clock
 FP64_PEAK_GFLOPS = 4 * 152 * 2.07
 # DRAM bytes (read + write) per launch of the headline kernel from one ncu
 # capture (dram__bytes_read.sum + dram__bytes_write.sum), valid only for the
 # library revision it was taken on; any other revision reports null.
-TRAFFIC_BYTES = {"campsolve 0.10 (sm_103a)": 51.665e6}
+TRAFFIC_BYTES = {"campsolve 0.10 (sm_103a)": 51.665e6,
+                 "campsolve 0.11 (sm_103a)": 51.747e6}
 
 
 def peaks():
@@ -514,6 +516,10 @@ def main():
                          "persistent multi-mechanism batch as the step; fused / newton: the "
                          "in-kernel assembly or the device Newton corrector alone (for "
                          "profiling)")
+    ap.add_argument("--ordering", type=int, default=None, choices=[0, 1, 2],
+                    help="cell ordering: 0 index order, 1 hardest first ordered inside the "
+                         "solve launch, 2 hardest first by a separate pass (default: the "
+                         "library's)")
     ap.add_argument("--skip-extras", action="store_true",
                     help="time the device solve only (no e2e, CPU baseline or mixed side run)")
     args = ap.parse_args()
@@ -550,6 +556,9 @@ def main():
     C = cb.cells
     solver = camp.Solver(m.row_ptr, m.col_idx)
     arr_desc = set_arrangement(camp, solver, args.arrangement)
+    if args.ordering is not None:
+        solver.set_ordering(args.ordering)
+    ordering = args.ordering if args.ordering is not None else DEFAULT_ORDERING
     A = torch.as_tensor(cb.A_vals, device=dev)
     b = torch.as_tensor(cb.b, device=dev)
     x = torch.empty((C, m.n), dtype=torch.float64, device=dev)
@@ -623,6 +632,8 @@ def main():
             "config": {"workload": synth.WORKLOADS[WORKLOAD_ID][0], "cells": C,
                        "n": m.n, "nnz": m.nnz, "tol": tol, "maxit": maxit,
                        "mode": args.mode, "arrangement": arr_desc,
+                       "ordering": ["index", "hardest first, in the solve launch",
+                                    "hardest first, separate pass"][ordering],
                        "l2": "flushed between timed steps (512 MB write)",
                        "iters_max": int(iters.max()), "iters_mean": float(iters.mean()),
                        "converged": int((status == 0).sum())},
@@ -637,7 +648,8 @@ def main():
                              "frac": nbytes / kernel_s / 1e9 / hbm_peak,
                              "peak_source": hbm_src},
             "e2e": e2e,
-            "gpu_launches": args.steps,
+            # the classify and scatter pass adds two launches per solve
+            "gpu_launches": args.steps * (3 if ordering == 2 and args.mode == "fp64" else 1),
             "clocks": clk,
         }
         if args.mode == "mixed":

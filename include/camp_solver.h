@@ -122,15 +122,32 @@ camp_status camp_solver_set_arrangement(camp_solver_t h, int arrangement,
                                         int warps_per_block);
 
 /*
- * Cell ordering for the warp arrangement: 0 (default) solves cells in index
- * order; 1 first estimates each cell's difficulty (the largest departure of
- * a diagonal entry from one, max_i |A_ii - 1|, which for A = I - gamma J is
- * gamma times the largest loss rate) and hands cells to warps hardest first,
- * so the cells that share a warp need similar iteration counts and the last
- * groups of the launch are short.  Results are identical either way (a
- * cell's solve does not depend on its neighbours); ordering adds a memset
- * and two small launches and device scratch of about 5 bytes per cell
- * (allocated on first use, grown on demand).
+ * Cell ordering for the warp arrangement (Sec. 3.2: the cells that share a
+ * warp run in lockstep, so pairing cells of similar difficulty wastes fewer
+ * lanes).  The difficulty estimate of a cell is the largest departure of a
+ * diagonal entry from one, max_i |A_ii - 1| (for A = I - gamma J: gamma
+ * times the largest loss rate), binned on half octaves; cells are paired
+ * and handed to warps hardest first, and an ordered launch gives every warp
+ * of its first wave one group from each difficulty stratum so that every SM
+ * gets a mix.  Results are bitwise identical in every mode (a cell's solve
+ * does not depend on its neighbours).
+ *   0: index order.
+ *   1 (default): the solve launch orders the cells itself (a cooperative
+ *      launch: every CTA classifies a share of the cells, one grid barrier,
+ *      then each warp waits for its group's order entries).  The estimate
+ *      reads the whole diagonal on the handle's first ordered solve and every
+ *      64th; in between only the (up to 8) rows where it peaked, picked on
+ *      the host from the counts of that full read (copied back without
+ *      blocking).  Device scratch: 8 bytes per cell plus 4 per row.
+ *      Solves on other streams (camp_solver_solve_host's chunks) and
+ *      launches whose warp regions cannot lend the ordering 2,576 bytes of
+ *      shared memory use index order or mode 2.  Under stream capture the
+ *      last picked rows are used as they are (allocate first: run one solve
+ *      before capturing).  Every wait of the launch is bounded (about a
+ *      second); if one runs out the launch completes with invalid results
+ *      and the handle's next solve call returns CAMP_ECUDA.
+ *   2: a separate classify and scatter pass (a memset and two small
+ *      launches before the solve; about 5 bytes of scratch per cell).
  */
 camp_status camp_solver_set_ordering(camp_solver_t h, int ordering);
 

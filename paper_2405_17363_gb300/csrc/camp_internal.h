@@ -51,8 +51,35 @@ struct WarpArgs {
   // ready for the next launch in stream order.  Null: static assignment.
   unsigned int *queue;
   // Optional cell order: group g's segment s solves cell order[g*k + s]
-  // (cells sorted by an estimate of their iteration count), or null.
+  // (cells sorted by an estimate of their iteration count), or null.  With
+  // an order, each SM should get a mix of hard and easy groups in the first
+  // wave.  ord_stride 0: every warp first solves group w*B + b (b its CTA
+  // of B, w its warp in the CTA; b reversed for odd w), so each CTA, hence
+  // each SM, takes one group from every stratum of B groups; the queue's
+  // tickets then take groups ord_wave + t (ord_wave = all warps of the grid)
+  // in order.  ord_stride > 0 (fewer groups than warps): ticket t takes
+  // group (t * ord_stride) mod ord_wave (ord_wave = ngroups, ord_stride
+  // coprime with it), so tickets taken together get mixed difficulty.
   const int *order;
+  int ord_wave, ord_stride;
+  // In-launch difficulty ordering (plain solve only; ord_ws null: off).  The
+  // launch is cooperative: every CTA first classifies a contiguous share of
+  // the cells by the largest |A_ii - 1| over the diagonal entries at pattern
+  // positions ord_rows[0 .. ord_nrows) (the whole diagonal, or the rows where
+  // the estimate peaked before), then, through two grid barriers, writes the
+  // hardest-first order to ord_out (= order) before any warp solves.
+  // ord_ws: kOrdWords ints (class totals, then the barrier counter), zero on
+  // entry and cleared by the launch's last warp; ord_cls: [cells] class |
+  // rank << 6 words; ord_hits (or null): per sampled row, the CTAs whose
+  // hardest cell peaked there; ord_err: a host-mapped word set to 1 if a
+  // barrier wait ran out of time (the launch's results are then invalid).
+  int *ord_out;
+  int *ord_ws;
+  int *ord_cls;
+  const int *ord_rows;
+  int ord_nrows;
+  unsigned *ord_hits;
+  int *ord_err;
   // Fused assembly (assemble_bicgstab_kernel only): the cell's matrix is
   // built in shared memory as A = I - gamma J(conc) instead of read from A.
   // Lane sl runs tcount terms p: J[slot (tmeta >> 11) * Lc + sl] +=
@@ -118,6 +145,8 @@ struct GradArgs {
 };
 
 // Launchers (each returns the launch error, cudaSuccess on success).
+// plain solve; a cooperative launch when a.ord_ws is set (grid must then be
+// co-resident: at most SMs x the occupancy of the launch shape)
 cudaError_t launch_warp(int E, const WarpArgs &a, int warps_per_block,
                         int grid, size_t smem, cudaStream_t st);
 cudaError_t warp_set_smem(int E, size_t smem);
@@ -147,6 +176,23 @@ cudaError_t launch_difficulty_order(const double *A, int cells, int n, int nnz,
                                     cudaStream_t st);
 
 constexpr int kMaxE = 16;  // rows per lane supported by the warp kernel
+
+// Difficulty classes of the ordering (half octaves of max_i |A_ii - 1|) and
+// the in-launch ordering's workspace: class totals and one barrier counter.
+constexpr int kOrdClasses = 64;
+constexpr int kOrdWords = kOrdClasses + 1;
+// Cells one CTA classifies per pass of the in-launch ordering, and the
+// shared-memory bytes that ordering borrows from the CTA's warp regions
+// before they are used: histogram, class bases, the CTA's hardest key, and
+// one 64-bit (estimate, row) key per cell of a pass.
+constexpr int kOrdPiece = 256;
+constexpr size_t kOrdKeyOffset = (2 * kOrdClasses + 4) * sizeof(int);
+constexpr size_t kOrdSmemBytes = kOrdKeyOffset + kOrdPiece * sizeof(unsigned long long);
+// Rows the ordering samples once it has seen where the estimate peaks, and
+// how often (in ordered solves) it reads the whole diagonal again to re-pick.
+constexpr int kOrdSample = 8;
+constexpr unsigned kOrdRecalibrate = 64;
+constexpr int kOrdBatch = 8;  // diagonal loads a thread keeps in flight
 
 // Raise a kernel's dynamic shared-memory limit to the device maximum once per
 // (kernel, device): setting the attribute on every launch serialises

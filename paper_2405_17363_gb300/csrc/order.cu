@@ -14,16 +14,7 @@
 namespace camp {
 namespace {
 
-constexpr int kClasses = 64;
-// class of an estimate from its high word: half-octave index (exponent and
-// first fraction bit), largest first; estimates >= 12 share class 0, those
-// below 2^-29 (and zero) class kClasses - 1
-__device__ __forceinline__ int class_of(unsigned hi) {
-  const int idx = (int)(hi >> 19);            // 2 * exponent + top fraction bit
-  const int top = ((1023 + 3) << 1) | 1;
-  const int c = top - idx;
-  return c < 0 ? 0 : (c >= kClasses ? kClasses - 1 : c);
-}
+constexpr int kClasses = kOrdClasses;
 
 __global__ void classify_kernel(const double *__restrict__ A, int cells, int n, int nnz,
                                 const int *__restrict__ diag, unsigned char *__restrict__ cls,
@@ -34,13 +25,12 @@ __global__ void classify_kernel(const double *__restrict__ A, int cells, int n, 
     const double *Ac = A + (size_t)c * nnz;
     unsigned worst = 0;  // high word of max |A_ii - 1| (non-negative: ordered as integers)
     for (int i = lane; i < n; i += 32) {
-      const double d = fabs(__ldg(Ac + __ldg(diag + i)) - 1.0);
-      const unsigned hi = (unsigned)((unsigned long long)__double_as_longlong(d) >> 32);
+      const unsigned hi = diag_departure_hi(__ldg(Ac + __ldg(diag + i)));
       worst = hi > worst ? hi : worst;
     }
     worst = __reduce_max_sync(kFull, worst);
     if (lane == 0) {
-      const int k = class_of(worst);
+      const int k = difficulty_class(worst);
       cls[c] = (unsigned char)k;
       atomicAdd(counts + k, 1);
     }

@@ -319,10 +319,26 @@ struct camp_solver {
   cudaEvent_t h_in[kHostChunks] = {}, h_done[kHostChunks] = {}, h_start = nullptr;
   std::mutex mu;
   Mechanism mech;
-  // difficulty ordering (camp_solver_set_ordering): scratch grown on demand
-  int ordering = 0;
+  // difficulty ordering (camp_solver_set_ordering): scratch grown on demand;
+  // the in-launch ordering's workspace follows the queue pairs in d_queue,
+  // its time-out word is host-mapped (allocated on first use)
+  int ordering = 1;
   void *d_order_scratch = nullptr;
   size_t order_cap = 0;  // bytes
+  int *h_ord_err = nullptr, *d_ord_err = nullptr;
+  // rows the in-launch ordering samples: picked on the host from the peak
+  // rows a full-diagonal ("calibration") launch records, read back without
+  // blocking (pinned copy + event); nsamp 0: no sample yet
+  unsigned *d_hits = nullptr, *h_hits = nullptr;
+  // in-launch order ([cells] entries, all zero between launches) and the
+  // class words of CTAs whose share exceeds one pass ([cells])
+  int *d_ord = nullptr;
+  size_t ord_cap = 0;  // cells
+  int *d_samp = nullptr;
+  int nsamp = 0;
+  cudaEvent_t ev_hits = nullptr;
+  bool hits_pending = false;
+  unsigned ordered_solves = 0;
 };
 
 namespace {
@@ -419,6 +435,66 @@ size_t block_smem(int n, int nnz, int cpb, int threads) {
           3 * (size_t)cpb) * 8;
 }
 
+// Stride of the first wave's ticket-to-group map: coprime with the wave (a
+// bijection) and near the golden section of it, so that any run of
+// consecutive tickets lands on groups spread over the whole difficulty range.
+int spread_stride(int wave) {
+  if (wave <= 2) return 1;
+  const int s0 = (int)(0.6180339887 * wave);
+  for (int d = 0; d < wave; ++d) {
+    for (int s : {s0 - d, s0 + d})
+      if (s >= 1 && s < wave && std::gcd(s, wave) == 1) return s;
+  }
+  return 1;
+}
+
+// Device and host state of the in-launch ordering, allocated on first use:
+// the host-mapped time-out word, the peak-row counts (device and pinned
+// host copies), the sampled positions and the read-back event.
+cudaError_t ordering_state(camp_solver_t h) {
+  cudaError_t e = cudaSuccess;
+  if (!h->h_ord_err) {
+    if ((e = cudaHostAlloc(&h->h_ord_err, sizeof(int), cudaHostAllocMapped)) != cudaSuccess)
+      return e;
+    *h->h_ord_err = 0;
+    if ((e = cudaHostGetDevicePointer(&h->d_ord_err, h->h_ord_err, 0)) != cudaSuccess) return e;
+  }
+  if (h->n > kOrdSample && !h->ev_hits) {
+    if ((e = cudaMalloc(&h->d_hits, (size_t)h->n * sizeof(unsigned))) != cudaSuccess) return e;
+    if ((e = cudaMalloc(&h->d_samp, kOrdSample * sizeof(int))) != cudaSuccess) return e;
+    if ((e = cudaHostAlloc(&h->h_hits, (size_t)h->n * sizeof(unsigned), cudaHostAllocDefault)) !=
+        cudaSuccess)
+      return e;
+    if ((e = cudaEventCreateWithFlags(&h->ev_hits, cudaEventDisableTiming)) != cudaSuccess)
+      return e;
+  }
+  return cudaSuccess;
+}
+
+// Once a calibration launch's peak-row counts have reached the host, sample
+// the (up to kOrdSample) rows where the most CTAs' hardest cells peaked.
+cudaError_t pick_sample(camp_solver_t h, cudaStream_t st) {
+  if (!h->hits_pending) return cudaSuccess;
+  cudaError_t e = cudaEventQuery(h->ev_hits);
+  if (e == cudaErrorNotReady) return cudaSuccess;
+  if (e != cudaSuccess) return e;
+  h->hits_pending = false;
+  std::vector<int> rows;
+  for (int i = 0; i < h->n; ++i)
+    if (h->h_hits[i]) rows.push_back(i);
+  std::stable_sort(rows.begin(), rows.end(),
+                   [&](int p, int q) { return h->h_hits[p] > h->h_hits[q]; });
+  if (rows.size() > (size_t)kOrdSample) rows.resize(kOrdSample);
+  if (rows.empty()) return cudaSuccess;
+  int pos[kOrdSample];
+  for (size_t j = 0; j < rows.size(); ++j) pos[j] = h->fwd.diag[rows[j]];
+  // a pageable source: the copy is staged before the call returns
+  e = cudaMemcpyAsync(h->d_samp, pos, rows.size() * sizeof(int), cudaMemcpyHostToDevice, st);
+  if (e != cudaSuccess) return e;
+  h->nsamp = (int)rows.size();
+  return cudaSuccess;
+}
+
 camp_status do_solve(camp_solver_t h, int cells, const double *A_vals,
                      const double *b, double *x, double tol, int maxit,
                      int *iters_out, double *resid_out, int *status_out,
@@ -433,6 +509,15 @@ camp_status do_solve(camp_solver_t h, int cells, const double *A_vals,
     return fail(CAMP_EINVAL, "null array pointer");
   cudaError_t e = cudaSetDevice(h->device);
   if (e != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
+  if (h->h_ord_err && *(volatile int *)h->h_ord_err) {
+    // the timed-out launch may have left order entries or class totals set
+    cudaStreamSynchronize(h->stream);
+    *(volatile int *)h->h_ord_err = 0;
+    if (h->d_ord) cudaMemset(h->d_ord, 0, h->ord_cap * sizeof(int));
+    cudaMemset(h->d_queue + 2 * (1 + kHostSolveStreams), 0, kOrdWords * sizeof(int));
+    return fail(CAMP_ECUDA, "a wait of an earlier ordered solve timed out: "
+                            "that solve's results are invalid");
+  }
   View &v = (flags & CAMP_TRANSPOSE) ? h->tr : h->fwd;
 
   int arr = h->arrangement;
@@ -472,9 +557,30 @@ camp_status do_solve(camp_solver_t h, int cells, const double *A_vals,
     a.x0_given = (flags & CAMP_X0_GIVEN) ? 1 : 0;
     a.queue = h->d_queue + 2 * queue_slot;
     a.order = nullptr;
+    bool calibrate = false;
+    int occ = 0;
+    e = warp_occupancy(E, wpb, smem, &occ);
+    if (e != cudaSuccess) return cuda_fail(e, "occupancy");
+    if (occ < 1) occ = 1;
+    // Ordering 1 runs inside the (cooperative) solve launch; it borrows
+    // kOrdSmemBytes of the warp regions before they are used.  Ordering 2, or
+    // 1 where that does not fit, runs the separate classify and scatter pass.
+    // Only the handle's own stream orders (one workspace per handle).
     if (h->ordering && cells > 1 && queue_slot == 0) {
+      const bool inl = h->ordering == 1 && smem - sched_smem_bytes(S->L * Lc) >= kOrdSmemBytes;
+      if (inl && (size_t)cells > h->ord_cap) {
+        cudaFree(h->d_ord);
+        h->d_ord = nullptr;
+        h->ord_cap = 0;
+        if ((e = cudaMalloc(&h->d_ord, (size_t)cells * 2 * sizeof(int))) != cudaSuccess)
+          return fail(CAMP_ENOMEM, "ordering scratch: %s", cudaGetErrorString(e));
+        // the entries start (and are left by every launch) all zero
+        if ((e = cudaMemsetAsync(h->d_ord, 0, (size_t)cells * sizeof(int), st)) != cudaSuccess)
+          return cuda_fail(e, "ordering scratch");
+        h->ord_cap = (size_t)cells;
+      }
       const size_t need = difficulty_scratch_bytes(cells);
-      if (need > h->order_cap) {
+      if (!inl && need > h->order_cap) {
         cudaFree(h->d_order_scratch);
         h->d_order_scratch = nullptr;
         h->order_cap = 0;
@@ -482,21 +588,67 @@ camp_status do_solve(camp_solver_t h, int cells, const double *A_vals,
           return fail(CAMP_ENOMEM, "ordering scratch: %s", cudaGetErrorString(e));
         h->order_cap = need;
       }
-      // the diagonal is the same in both orientations: forward positions
-      int *order = nullptr;
-      e = launch_difficulty_order(A_vals, cells, h->fwd.n, h->fwd.nnz, h->fwd.d_diag,
-                                  h->d_order_scratch, &order, st);
-      if (e != cudaSuccess) return cuda_fail(e, "difficulty ordering");
-      a.order = order;
+      if (inl) {
+        if ((e = ordering_state(h)) != cudaSuccess) return cuda_fail(e, "ordering state");
+        a.ord_out = h->d_ord;
+        a.ord_cls = h->d_ord + h->ord_cap;
+        a.ord_ws = (int *)(h->d_queue + 2 * (1 + kHostSolveStreams));
+        a.ord_err = h->d_ord_err;
+        a.order = a.ord_out;
+        // the diagonal is the same in both orientations: forward positions
+        a.ord_rows = h->fwd.d_diag;
+        a.ord_nrows = h->n;
+        // under stream capture the sample stays as it is (no host read-back)
+        cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+        if ((e = cudaStreamIsCapturing(st, &cap)) != cudaSuccess) return cuda_fail(e, "capture query");
+        if (h->n > kOrdSample && cap != cudaStreamCaptureStatusNone) {
+          if (h->nsamp > 0) {
+            a.ord_rows = h->d_samp;
+            a.ord_nrows = h->nsamp;
+          }
+        } else if (h->n > kOrdSample) {
+          if ((e = pick_sample(h, st)) != cudaSuccess) return cuda_fail(e, "ordering sample");
+          if (!h->hits_pending && (h->nsamp == 0 || h->ordered_solves % kOrdRecalibrate == 0)) {
+            calibrate = true;
+            if ((e = cudaMemsetAsync(h->d_hits, 0, (size_t)h->n * sizeof(unsigned), st)) !=
+                cudaSuccess)
+              return cuda_fail(e, "ordering hits");
+            a.ord_hits = h->d_hits;
+          } else if (h->nsamp > 0) {
+            a.ord_rows = h->d_samp;
+            a.ord_nrows = h->nsamp;
+          }
+          ++h->ordered_solves;
+        }
+      } else {
+        int *order = nullptr;
+        e = launch_difficulty_order(A_vals, cells, h->fwd.n, h->fwd.nnz, h->fwd.d_diag,
+                                    h->d_order_scratch, &order, st);
+        if (e != cudaSuccess) return cuda_fail(e, "difficulty ordering");
+        a.order = order;
+      }
     }
-    int occ = 0;
-    e = warp_occupancy(E, wpb, smem, &occ);
-    if (e != cudaSuccess) return cuda_fail(e, "occupancy");
-    if (occ < 1) occ = 1;
     const int need = (a.ngroups + wpb - 1) / wpb;
     const int grid = std::max(1, std::min(need, h->sms * occ));
+    if (a.order) {
+      if (a.ngroups >= grid * wpb) {
+        a.ord_wave = grid * wpb;  // stratified first wave, then tickets
+        a.ord_stride = 0;
+      } else {
+        a.ord_wave = a.ngroups;
+        a.ord_stride = spread_stride(a.ngroups);
+      }
+    }
     e = launch_warp(E, a, wpb, grid, smem, st);
     if (e != cudaSuccess) return cuda_fail(e, "warp kernel launch");
+    if (calibrate) {
+      // the peak rows come back without blocking; a later solve picks them up
+      e = cudaMemcpyAsync(h->h_hits, h->d_hits, (size_t)h->n * sizeof(unsigned),
+                          cudaMemcpyDeviceToHost, st);
+      if (e == cudaSuccess) e = cudaEventRecord(h->ev_hits, st);
+      if (e != cudaSuccess) return cuda_fail(e, "ordering hits read-back");
+      h->hits_pending = true;
+    }
     return CAMP_OK;
   }
 
@@ -525,7 +677,7 @@ camp_status do_solve(camp_solver_t h, int cells, const double *A_vals,
 extern "C" {
 
 const char *camp_last_error(void) { return g_err.c_str(); }
-const char *camp_version(void) { return "campsolve 0.10 (sm_103a)"; }
+const char *camp_version(void) { return "campsolve 0.11 (sm_103a)"; }
 
 camp_status camp_schedule_build(int n, int nnz, const int *row_ptr,
                                 const int *col_idx, int lanes_per_cell,
@@ -625,7 +777,8 @@ camp_status camp_solver_create(camp_solver_t *out, int n, int nnz,
       (e = upload(&t.d_diag, t.diag)) != cudaSuccess ||
       (e = upload(&t.d_perm, t.perm)) != cudaSuccess ||
       (e = upload(&h->d_row_of, row_of)) != cudaSuccess ||
-      (e = upload(&h->d_queue, std::vector<unsigned int>(2 * (1 + kHostSolveStreams), 0u))) != cudaSuccess) {
+      (e = upload(&h->d_queue, std::vector<unsigned int>(2 * (1 + kHostSolveStreams) + kOrdWords,
+                                                          0u))) != cudaSuccess) {
     free_view(h->fwd);
     free_view(h->tr);
     cudaFree(h->d_row_of);
@@ -647,6 +800,12 @@ camp_status camp_solver_destroy(camp_solver_t h) {
   cudaFree(h->d_row_of);
   cudaFree(h->d_queue);
   cudaFree(h->d_order_scratch);
+  if (h->h_ord_err) cudaFreeHost(h->h_ord_err);
+  if (h->h_hits) cudaFreeHost(h->h_hits);
+  cudaFree(h->d_hits);
+  cudaFree(h->d_ord);
+  cudaFree(h->d_samp);
+  if (h->ev_hits) cudaEventDestroy(h->ev_hits);
   cudaFree(h->h_dA); cudaFree(h->h_db); cudaFree(h->h_dx);
   cudaFree(h->h_dres); cudaFree(h->h_dit); cudaFree(h->h_dst);
   for (auto &s : h->h_streams) if (s) cudaStreamDestroy(s);
@@ -697,7 +856,7 @@ camp_status camp_solver_set_arrangement(camp_solver_t h, int arrangement,
 
 camp_status camp_solver_set_ordering(camp_solver_t h, int ordering) {
   if (!h) return fail(CAMP_EINVAL, "null solver handle");
-  if (ordering != 0 && ordering != 1) return fail(CAMP_EINVAL, "ordering must be 0 or 1");
+  if (ordering < 0 || ordering > 2) return fail(CAMP_EINVAL, "ordering must be 0, 1 or 2");
   h->ordering = ordering;
   return CAMP_OK;
 }

@@ -9,6 +9,21 @@ namespace camp {
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int kSpmvUnroll = 4;  // SpMV pipeline block (slots per lane)
 
+// Difficulty class of a cell from the high word of its estimate
+// max_i |A_ii - 1| (a non-negative double, so its high words order as
+// integers): the half-octave index (exponent and first fraction bit),
+// largest first; estimates >= 12 share class 0, those below 2^-29 (and zero)
+// the last class.
+__device__ __forceinline__ int difficulty_class(unsigned hi) {
+  const int idx = (int)(hi >> 19);  // 2 * biased exponent + top fraction bit
+  const int top = ((1023 + 3) << 1) | 1;
+  const int c = top - idx;
+  return c < 0 ? 0 : (c >= kOrdClasses ? kOrdClasses - 1 : c);
+}
+__device__ __forceinline__ unsigned diag_departure_hi(double aii) {
+  return (unsigned)((unsigned long long)__double_as_longlong(fabs(aii - 1.0)) >> 32);
+}
+
 __device__ __forceinline__ bool is_finite_bits(double v) {
   const unsigned long long u = (unsigned long long)__double_as_longlong(v);
   return ((u >> 52) & 0x7ffull) != 0x7ffull;

@@ -183,22 +183,67 @@ def test_initial_guess_and_transpose(camp, cuda):
 @pytest.mark.parametrize("wid", [1, 4])
 def test_difficulty_ordering_gives_identical_results(camp, cuda, wid):
     """Handing cells to warps hardest first changes which cells share a warp,
-    never a cell's result: bitwise identical outputs, transposed solves too."""
+    never a cell's result: bitwise identical outputs, transposed solves too,
+    for both the in-launch ordering (1) and the separate pass (2).  The batch
+    sizes change from call to call (ragged, tiny, larger than one ordering
+    piece per CTA), so a workspace or order entry left over from the previous
+    launch would misplace cells."""
     import torch
     cbs, tol, maxit = synth.workload(wid, cells=2001)
+    cb = cbs[0]
+    m = cb.mech
+    A0 = torch.as_tensor(cb.A_vals, device=cuda)
+    b0 = torch.as_tensor(cb.b, device=cuda)
+    s = camp.Solver(m.row_ptr, m.col_idx)
+    for cells in (2001, 2, 1500, 33, 2001, 2001 * 90):
+        reps = (cells + 2000) // 2001
+        A = A0.repeat(reps, 1)[:cells].contiguous()
+        b = b0.repeat(reps, 1)[:cells].contiguous()
+        for transpose in (False, True):
+            s.set_ordering(0)
+            ref = [t.clone() for t in s.solve(A, b, tol, maxit, transpose=transpose)]
+            for mode in (1, 2, 1):
+                s.set_ordering(mode)
+                got = s.solve(A, b, tol, maxit, transpose=transpose)
+                torch.cuda.synchronize()
+                for r, g in zip(ref, got):
+                    assert torch.equal(r, g), (cells, transpose, mode)
+    s.close()
+
+
+def test_ordering_sample_and_recalibration(camp, cuda):
+    """The in-launch ordering reads the whole diagonal on its first ordered
+    solve, then only the rows where the estimate peaked, and the whole
+    diagonal again every 64 ordered solves: through 140 solves (two
+    recalibrations) every result stays bitwise that of index order.  A
+    mechanism with no more rows than the sample always reads them all."""
+    import torch
+    cbs, tol, maxit = synth.workload(1, cells=3001)
     cb = cbs[0]
     m = cb.mech
     A = torch.as_tensor(cb.A_vals, device=cuda)
     b = torch.as_tensor(cb.b, device=cuda)
     s = camp.Solver(m.row_ptr, m.col_idx)
-    for transpose in (False, True):
-        s.set_ordering(0)
-        ref = [t.clone() for t in s.solve(A, b, tol, maxit, transpose=transpose)]
-        s.set_ordering(1)
-        got = s.solve(A, b, tol, maxit, transpose=transpose)
-        torch.cuda.synchronize()
+    ref = [t.clone() for t in s.solve(A, b, tol, maxit)]
+    s.set_ordering(1)
+    for rep in range(140):
+        got = s.solve(A, b, tol, maxit, transpose=False)
+        if rep % 7 == 0:
+            torch.cuda.synchronize()
         for r, g in zip(ref, got):
-            assert torch.equal(r, g)
+            assert torch.equal(r, g), rep
+    s.close()
+    mech = synth.make_mechanism(6, 12, 5)
+    small = synth.make_cells(mech, 777, 6, gamma=(1e-4, 1e-1))
+    A = torch.as_tensor(small.A_vals, device=cuda)
+    b = torch.as_tensor(small.b, device=cuda)
+    s = camp.Solver(mech.row_ptr, mech.col_idx)
+    ref = [t.clone() for t in s.solve(A, b, tol, maxit)]
+    s.set_ordering(1)
+    for rep in range(3):
+        got = s.solve(A, b, tol, maxit)
+        for r, g in zip(ref, got):
+            assert torch.equal(r, g), rep
     s.close()
 
 
