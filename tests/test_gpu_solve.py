@@ -247,6 +247,48 @@ def test_ordering_sample_and_recalibration(camp, cuda):
     s.close()
 
 
+def test_ordered_solve_in_cuda_graph(camp, cuda):
+    """The ordered (cooperative) solve captured in a CUDA graph: replays give
+    bitwise the eager index-order results, also after the inputs change in
+    place (the order entries are cleared by every replay)."""
+    import torch
+    cbs, tol, maxit = synth.workload(1, cells=4000)
+    cb = cbs[0]
+    m = cb.mech
+    A = torch.as_tensor(cb.A_vals, device=cuda)
+    b = torch.as_tensor(cb.b, device=cuda)
+    s = camp.Solver(m.row_ptr, m.col_idx)
+    s.set_ordering(0)
+    ref = [t.clone() for t in s.solve(A, b, tol, maxit)]
+    ref2 = [t.clone() for t in s.solve(A.flip(0).contiguous(), b.flip(0).contiguous(), tol, maxit)]
+    s.set_ordering(1)
+    out = [torch.empty_like(t) for t in ref]
+    for _ in range(3):  # allocate the ordering state and pick the sampled rows
+        s.solve(A, b, tol, maxit, out=out)
+        torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    stream = torch.cuda.Stream()
+    stream.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(stream):
+        with torch.cuda.graph(g, stream=stream):
+            s.solve(A, b, tol, maxit, out=out)
+    torch.cuda.current_stream().wait_stream(stream)
+    for rep in range(3):
+        for t in out:
+            t.zero_()
+        g.replay()
+        torch.cuda.synchronize()
+        for r, o in zip(ref, out):
+            assert torch.equal(r, o), rep
+    A.copy_(A.flip(0).clone())
+    b.copy_(b.flip(0).clone())
+    g.replay()
+    torch.cuda.synchronize()
+    for r, o in zip(ref2, out):
+        assert torch.equal(r, o)
+    s.close()
+
+
 @pytest.mark.parametrize("n,R", [(400, 1000), (700, 1600)])
 def test_large_mechanisms(camp, cuda, n, R):
     """Mechanisms far beyond the benchmark's: 400 species (automatic choice:
