@@ -231,7 +231,19 @@ struct MixedArgs {
   int max_sweeps;
   float tol_in;
   int maxit_in;
+  // dynamic group queue and difficulty ordering, as in WarpArgs
+  unsigned int *queue;
+  const int *order;
+  int ord_wave, ord_stride;
+  int *ord_out;
+  int *ord_ws;
+  int *ord_cls;
+  const int *ord_rows;
+  int ord_nrows;
+  unsigned *ord_hits;
+  int *ord_err;
 };
+// a cooperative launch when a.ord_ws is set (grid at most SMs x occupancy)
 cudaError_t launch_mixed(int E, const MixedArgs &a, int warps_per_block,
                          int grid, size_t smem, cudaStream_t st);
 cudaError_t mixed_occupancy(int E, int warps_per_block, size_t smem, int *blocks);

@@ -37,16 +37,26 @@ __device__ __forceinline__ void mixed_body(const MixedArgs &a) {
   float *g32 = As32 + a.segA;
   float *o1 = g32 + a.segV;
   float *o2 = o1 + a.segV;
+  // in-launch difficulty ordering first: it borrows the start of the warp
+  // regions (and ends with a block barrier)
+  if (a.ord_ws) order_prologue(a, reinterpret_cast<int *>(smem_raw + sched_smem_bytes(nsch)));
   for (int i = sl; i < a.segV; i += Lc) {
     g64[i] = 0.0; o64[i] = 0.0; g32[i] = 0.0f; o1[i] = 0.0f; o2[i] = 0.0f;
   }
   __syncthreads();
   const SchedWord *sch = sch_s + sl;
   const int warps_total = gridDim.x * (blockDim.x >> 5);
+  constexpr int K = LC ? 32 / LC : 0;  // cells per warp (0: a.k)
 
-  for (int g = blockIdx.x * (blockDim.x >> 5) + warp; g < a.ngroups; g += warps_total) {
-    const int c = g * (LC ? 32 / LC : a.k) + seg;
-    const bool has = c < a.cells;
+  auto refine_group = [&](int g) {
+    const int pos = g * (K ? K : a.k) + seg;
+    const bool has = pos < a.cells;
+    // the order may have been written earlier in this launch (cell + 1 from
+    // the in-launch ordering): read it through L2, clamped in range
+    const int c = (has && a.order)
+                      ? (int)min((unsigned)(__ldcg(a.order + pos) - (a.ord_ws ? 1 : 0)),
+                                 (unsigned)a.cells - 1u)
+                      : pos;
     {  // stage A in slot order, FP64 and its FP32 rounding
       const double *Ac = a.A + (size_t)(has ? c : 0) * nnz;
       stage_scatter(Ac, a.dst, nnz, sl, Lc, has, [&](int t, double v) {
@@ -250,7 +260,23 @@ __device__ __forceinline__ void mixed_body(const MixedArgs &a) {
       }
     }
     __syncwarp();
+  };
+
+  if (!a.queue) {
+    for (int g = blockIdx.x * (blockDim.x >> 5) + warp; g < a.ngroups; g += warps_total)
+      refine_group(g);
+    return;
   }
+  // dynamic assignment (an ordered launch first gives every warp one group
+  // of a stratified wave)
+  bool first = true;
+  unsigned g = 0;
+  while (take_group(a, warp, lane, first, g)) {
+    const bool mine = await_order_entries(a, g, K ? K : a.k, lane);
+    refine_group((int)g);
+    if (mine) a.ord_out[g * (K ? K : a.k) + lane] = 0;
+  }
+  finish_queue(a, true, warps_total, lane);
 }
 
 template <int E>

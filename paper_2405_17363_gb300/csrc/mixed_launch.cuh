@@ -5,6 +5,12 @@
                                size_t smem, cudaStream_t st) {                  \
     cudaError_t e = ensure_max_smem((const void *)mixed_refine_kernel<E>);      \
     if (e != cudaSuccess) return e;                                             \
+    if (a.ord_ws) {                                                             \
+      void *args[] = {(void *)&a};                                              \
+      return cudaLaunchCooperativeKernel((const void *)mixed_refine_kernel<E>,  \
+                                         dim3(grid), dim3(wpb * 32), args,      \
+                                         smem, st);                             \
+    }                                                                           \
     mixed_refine_kernel<E><<<grid, wpb * 32, smem, st>>>(a);                    \
     return cudaGetLastError();                                                  \
   }                                                                             \

@@ -495,6 +495,117 @@ cudaError_t pick_sample(camp_solver_t h, cudaStream_t st) {
   return cudaSuccess;
 }
 
+// Difficulty ordering of a warp-packed solve on the handle's own stream (one
+// workspace per handle).  Ordering 1 runs inside the (cooperative) solve
+// launch, borrowing kOrdSmemBytes of the warp regions (smem_free bytes of
+// them) before they are used; ordering 2, or 1 where that does not fit, runs
+// the separate classify and scatter pass.  Fills the order fields of a
+// (WarpArgs or MixedArgs; a.cells, a.ngroups set); *calibrate tells the
+// caller to read the peak-row counts back after the launch.
+template <class Args>
+camp_status setup_ordering(camp_solver_t h, Args &a, const double *A_vals, size_t smem_free,
+                           cudaStream_t st, bool *calibrate) {
+  const int cells = a.cells;
+  *calibrate = false;
+  if (!h->ordering || cells <= 1) return CAMP_OK;
+  cudaError_t e = cudaSuccess;
+  const bool inl = h->ordering == 1 && smem_free >= kOrdSmemBytes;
+  if (inl && (size_t)cells > h->ord_cap) {
+    cudaFree(h->d_ord);
+    h->d_ord = nullptr;
+    h->ord_cap = 0;
+    if ((e = cudaMalloc(&h->d_ord, (size_t)cells * 2 * sizeof(int))) != cudaSuccess)
+      return fail(CAMP_ENOMEM, "ordering scratch: %s", cudaGetErrorString(e));
+    // the entries start (and are left by every launch) all zero
+    if ((e = cudaMemsetAsync(h->d_ord, 0, (size_t)cells * sizeof(int), st)) != cudaSuccess)
+      return cuda_fail(e, "ordering scratch");
+    h->ord_cap = (size_t)cells;
+  }
+  const size_t need = difficulty_scratch_bytes(cells);
+  if (!inl && need > h->order_cap) {
+    cudaFree(h->d_order_scratch);
+    h->d_order_scratch = nullptr;
+    h->order_cap = 0;
+    if ((e = cudaMalloc(&h->d_order_scratch, need)) != cudaSuccess)
+      return fail(CAMP_ENOMEM, "ordering scratch: %s", cudaGetErrorString(e));
+    h->order_cap = need;
+  }
+  if (!inl) {
+    int *order = nullptr;
+    e = launch_difficulty_order(A_vals, cells, h->fwd.n, h->fwd.nnz, h->fwd.d_diag,
+                                h->d_order_scratch, &order, st);
+    if (e != cudaSuccess) return cuda_fail(e, "difficulty ordering");
+    a.order = order;
+    return CAMP_OK;
+  }
+  if ((e = ordering_state(h)) != cudaSuccess) return cuda_fail(e, "ordering state");
+  a.ord_out = h->d_ord;
+  a.ord_cls = h->d_ord + h->ord_cap;
+  a.ord_ws = (int *)(h->d_queue + 2 * (1 + kHostSolveStreams));
+  a.ord_err = h->d_ord_err;
+  a.order = a.ord_out;
+  // the diagonal is the same in both orientations: forward positions
+  a.ord_rows = h->fwd.d_diag;
+  a.ord_nrows = h->n;
+  if (h->n <= kOrdSample) return CAMP_OK;
+  // under stream capture the sample stays as it is (no host read-back)
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if ((e = cudaStreamIsCapturing(st, &cap)) != cudaSuccess) return cuda_fail(e, "capture query");
+  if (cap == cudaStreamCaptureStatusNone) {
+    if ((e = pick_sample(h, st)) != cudaSuccess) return cuda_fail(e, "ordering sample");
+    if (!h->hits_pending && (h->nsamp == 0 || h->ordered_solves % kOrdRecalibrate == 0)) {
+      *calibrate = true;
+      if ((e = cudaMemsetAsync(h->d_hits, 0, (size_t)h->n * sizeof(unsigned), st)) != cudaSuccess)
+        return cuda_fail(e, "ordering hits");
+      a.ord_hits = h->d_hits;
+    }
+    ++h->ordered_solves;
+  }
+  if (!*calibrate && h->nsamp > 0) {
+    a.ord_rows = h->d_samp;
+    a.ord_nrows = h->nsamp;
+  }
+  return CAMP_OK;
+}
+
+// After a calibrating launch: the peak-row counts come back without
+// blocking; a later solve picks the rows up.
+camp_status read_back_hits(camp_solver_t h, cudaStream_t st) {
+  cudaError_t e = cudaMemcpyAsync(h->h_hits, h->d_hits, (size_t)h->n * sizeof(unsigned),
+                                  cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaEventRecord(h->ev_hits, st);
+  if (e != cudaSuccess) return cuda_fail(e, "ordering hits read-back");
+  h->hits_pending = true;
+  return CAMP_OK;
+}
+
+// The first wave of an ordered launch (WarpArgs::ord_wave): stratified when
+// every warp of the grid gets a group, else tickets spread over the order.
+template <class Args>
+void set_wave(Args &a, int grid, int wpb) {
+  if (!a.order) return;
+  if (a.ngroups >= grid * wpb) {
+    a.ord_wave = grid * wpb;
+    a.ord_stride = 0;
+  } else {
+    a.ord_wave = a.ngroups;
+    a.ord_stride = spread_stride(a.ngroups);
+  }
+}
+
+// A bounded wait of an earlier in-launch ordering ran out (the host-mapped
+// word is set): that launch may have left order entries or class totals
+// set, so clear them, and report the earlier solve's results as invalid.
+bool ordering_timed_out(camp_solver_t h) {
+  if (!h->h_ord_err || !*(volatile int *)h->h_ord_err) return false;
+  cudaStreamSynchronize(h->stream);
+  *(volatile int *)h->h_ord_err = 0;
+  if (h->d_ord) cudaMemset(h->d_ord, 0, h->ord_cap * sizeof(int));
+  cudaMemset(h->d_queue + 2 * (1 + kHostSolveStreams), 0, kOrdWords * sizeof(int));
+  fail(CAMP_ECUDA, "a wait of an earlier ordered solve timed out: that solve's results are invalid");
+  return true;
+}
+
 camp_status do_solve(camp_solver_t h, int cells, const double *A_vals,
                      const double *b, double *x, double tol, int maxit,
                      int *iters_out, double *resid_out, int *status_out,
@@ -509,15 +620,7 @@ camp_status do_solve(camp_solver_t h, int cells, const double *A_vals,
     return fail(CAMP_EINVAL, "null array pointer");
   cudaError_t e = cudaSetDevice(h->device);
   if (e != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
-  if (h->h_ord_err && *(volatile int *)h->h_ord_err) {
-    // the timed-out launch may have left order entries or class totals set
-    cudaStreamSynchronize(h->stream);
-    *(volatile int *)h->h_ord_err = 0;
-    if (h->d_ord) cudaMemset(h->d_ord, 0, h->ord_cap * sizeof(int));
-    cudaMemset(h->d_queue + 2 * (1 + kHostSolveStreams), 0, kOrdWords * sizeof(int));
-    return fail(CAMP_ECUDA, "a wait of an earlier ordered solve timed out: "
-                            "that solve's results are invalid");
-  }
+  if (ordering_timed_out(h)) return CAMP_ECUDA;
   View &v = (flags & CAMP_TRANSPOSE) ? h->tr : h->fwd;
 
   int arr = h->arrangement;
@@ -562,94 +665,17 @@ camp_status do_solve(camp_solver_t h, int cells, const double *A_vals,
     e = warp_occupancy(E, wpb, smem, &occ);
     if (e != cudaSuccess) return cuda_fail(e, "occupancy");
     if (occ < 1) occ = 1;
-    // Ordering 1 runs inside the (cooperative) solve launch; it borrows
-    // kOrdSmemBytes of the warp regions before they are used.  Ordering 2, or
-    // 1 where that does not fit, runs the separate classify and scatter pass.
-    // Only the handle's own stream orders (one workspace per handle).
-    if (h->ordering && cells > 1 && queue_slot == 0) {
-      const bool inl = h->ordering == 1 && smem - sched_smem_bytes(S->L * Lc) >= kOrdSmemBytes;
-      if (inl && (size_t)cells > h->ord_cap) {
-        cudaFree(h->d_ord);
-        h->d_ord = nullptr;
-        h->ord_cap = 0;
-        if ((e = cudaMalloc(&h->d_ord, (size_t)cells * 2 * sizeof(int))) != cudaSuccess)
-          return fail(CAMP_ENOMEM, "ordering scratch: %s", cudaGetErrorString(e));
-        // the entries start (and are left by every launch) all zero
-        if ((e = cudaMemsetAsync(h->d_ord, 0, (size_t)cells * sizeof(int), st)) != cudaSuccess)
-          return cuda_fail(e, "ordering scratch");
-        h->ord_cap = (size_t)cells;
-      }
-      const size_t need = difficulty_scratch_bytes(cells);
-      if (!inl && need > h->order_cap) {
-        cudaFree(h->d_order_scratch);
-        h->d_order_scratch = nullptr;
-        h->order_cap = 0;
-        if ((e = cudaMalloc(&h->d_order_scratch, need)) != cudaSuccess)
-          return fail(CAMP_ENOMEM, "ordering scratch: %s", cudaGetErrorString(e));
-        h->order_cap = need;
-      }
-      if (inl) {
-        if ((e = ordering_state(h)) != cudaSuccess) return cuda_fail(e, "ordering state");
-        a.ord_out = h->d_ord;
-        a.ord_cls = h->d_ord + h->ord_cap;
-        a.ord_ws = (int *)(h->d_queue + 2 * (1 + kHostSolveStreams));
-        a.ord_err = h->d_ord_err;
-        a.order = a.ord_out;
-        // the diagonal is the same in both orientations: forward positions
-        a.ord_rows = h->fwd.d_diag;
-        a.ord_nrows = h->n;
-        // under stream capture the sample stays as it is (no host read-back)
-        cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
-        if ((e = cudaStreamIsCapturing(st, &cap)) != cudaSuccess) return cuda_fail(e, "capture query");
-        if (h->n > kOrdSample && cap != cudaStreamCaptureStatusNone) {
-          if (h->nsamp > 0) {
-            a.ord_rows = h->d_samp;
-            a.ord_nrows = h->nsamp;
-          }
-        } else if (h->n > kOrdSample) {
-          if ((e = pick_sample(h, st)) != cudaSuccess) return cuda_fail(e, "ordering sample");
-          if (!h->hits_pending && (h->nsamp == 0 || h->ordered_solves % kOrdRecalibrate == 0)) {
-            calibrate = true;
-            if ((e = cudaMemsetAsync(h->d_hits, 0, (size_t)h->n * sizeof(unsigned), st)) !=
-                cudaSuccess)
-              return cuda_fail(e, "ordering hits");
-            a.ord_hits = h->d_hits;
-          } else if (h->nsamp > 0) {
-            a.ord_rows = h->d_samp;
-            a.ord_nrows = h->nsamp;
-          }
-          ++h->ordered_solves;
-        }
-      } else {
-        int *order = nullptr;
-        e = launch_difficulty_order(A_vals, cells, h->fwd.n, h->fwd.nnz, h->fwd.d_diag,
-                                    h->d_order_scratch, &order, st);
-        if (e != cudaSuccess) return cuda_fail(e, "difficulty ordering");
-        a.order = order;
-      }
+    if (queue_slot == 0) {
+      const camp_status rs = setup_ordering(h, a, A_vals, smem - sched_smem_bytes(S->L * Lc), st,
+                                            &calibrate);
+      if (rs != CAMP_OK) return rs;
     }
     const int need = (a.ngroups + wpb - 1) / wpb;
     const int grid = std::max(1, std::min(need, h->sms * occ));
-    if (a.order) {
-      if (a.ngroups >= grid * wpb) {
-        a.ord_wave = grid * wpb;  // stratified first wave, then tickets
-        a.ord_stride = 0;
-      } else {
-        a.ord_wave = a.ngroups;
-        a.ord_stride = spread_stride(a.ngroups);
-      }
-    }
+    set_wave(a, grid, wpb);
     e = launch_warp(E, a, wpb, grid, smem, st);
     if (e != cudaSuccess) return cuda_fail(e, "warp kernel launch");
-    if (calibrate) {
-      // the peak rows come back without blocking; a later solve picks them up
-      e = cudaMemcpyAsync(h->h_hits, h->d_hits, (size_t)h->n * sizeof(unsigned),
-                          cudaMemcpyDeviceToHost, st);
-      if (e == cudaSuccess) e = cudaEventRecord(h->ev_hits, st);
-      if (e != cudaSuccess) return cuda_fail(e, "ordering hits read-back");
-      h->hits_pending = true;
-    }
-    return CAMP_OK;
+    return calibrate ? read_back_hits(h, st) : CAMP_OK;
   }
 
   // block arrangement
@@ -1267,6 +1293,7 @@ camp_status camp_solver_solve_mixed(camp_solver_t h, int cells,
     return fail(CAMP_EINVAL, "null array pointer");
   cudaError_t e = cudaSetDevice(h->device);
   if (e != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
+  if (ordering_timed_out(h)) return CAMP_ECUDA;
   View &v = h->fwd;
   int Lc = (h->arrangement == CAMP_ARR_WARP) ? h->lanes : auto_lanes(v.n, kAutoRowsPerLaneMixed);
   if (Lc == 0) return fail(CAMP_EUNSUPPORTED, "no warp arrangement fits n=%d", v.n);
@@ -1288,14 +1315,25 @@ camp_status camp_solver_solve_mixed(camp_solver_t h, int cells,
   a.dst = S->d_dst; a.padfrom = S->d_padfrom; a.dslot = S->d_dslot;
   a.tol = tol; a.max_sweeps = max_sweeps; a.tol_in = (float)tol_inner;
   a.maxit_in = maxit_inner;
+  a.queue = h->d_queue;  // the handle's own stream: queue pair 0
+  // Ordering pays here only by pairing: with one cell per warp (the automatic
+  // choice above 48 species) its prologue costs more than hardest-first saves
+  // (131 against 125 us at 80 species x 10,000 cells).
+  bool calibrate = false;
+  if (a.k > 1) {
+    const camp_status rs = setup_ordering(h, a, A_vals, smem - sched_smem_bytes(S->L * Lc),
+                                          h->stream, &calibrate);
+    if (rs != CAMP_OK) return rs;
+  }
   int occ = 0;
   if ((e = mixed_occupancy(E, wpb, smem, &occ)) != cudaSuccess) return cuda_fail(e, "occupancy");
   if (occ < 1) occ = 1;
   const int need = (a.ngroups + wpb - 1) / wpb;
   const int grid = std::max(1, std::min(need, h->sms * occ));
+  set_wave(a, grid, wpb);
   if ((e = launch_mixed(E, a, wpb, grid, smem, h->stream)) != cudaSuccess)
     return cuda_fail(e, "mixed kernel launch");
-  return CAMP_OK;
+  return calibrate ? read_back_hits(h, h->stream) : CAMP_OK;
 }
 
 

@@ -415,4 +415,201 @@ __device__ __forceinline__ double seg_sum_x(double v, int Lc) {
   else return seg_sum_exact(v, Lc);
 }
 
+// Grid barrier of a cooperative launch, bounded in time: the CTA's threads
+// meet, thread 0 publishes the CTA's writes and counts it in, then waits
+// until the counter reaches target.  A wait longer than ~2^31 clocks (about a
+// second; the CTAs of a cooperative launch are all resident, so a legitimate
+// wait is microseconds) sets the host-mapped error word and goes on.
+__device__ __forceinline__ void grid_barrier_bounded(unsigned *ctr, unsigned target,
+                                                            int *err) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    atomicAdd(ctr, 1u);
+    const long long t0 = clock64();
+    for (;;) {
+      unsigned v;
+      asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(ctr) : "memory");
+      if (v >= target) break;
+      if (clock64() - t0 > (1ll << 31)) {
+        if (err) {
+          *(volatile int *)err = 1;
+          __threadfence_system();
+        }
+        break;
+      }
+      __nanosleep(64);
+    }
+    __threadfence();
+  }
+  __syncthreads();
+}
+
+// In-launch difficulty ordering (run by every CTA of a cooperative solve
+// launch before it solves; Args: WarpArgs or MixedArgs).  The estimate, the classes and the hardest-first
+// order are those of the separate ordering pass: max_i |A_ii - 1| binned on
+// half octaves, here over the sampled diagonal rows.  Each CTA classifies a
+// contiguous share of the cells, counts them per class in shared memory and
+// reserves its range inside each class with one global atomic per class;
+// after a grid barrier it turns the class totals into class starts and
+// writes its cells' order entries (cell + 1).  A warp that takes a group
+// waits for the group's entries (written by whichever CTAs own those cells,
+// all resident and past the barrier) and clears them once it has read them,
+// so the order is all zero again for the next launch.
+// sm: kOrdSmemBytes of this CTA's shared memory not yet in use.
+template <class Args>
+__device__ __forceinline__ void order_prologue(const Args &a, int *sm) {
+  int *hist = sm;                       // per class: count, then class start
+  int *base = sm + kOrdClasses;         // per class: this CTA's offset inside it
+  unsigned long long *bkey = reinterpret_cast<unsigned long long *>(sm + 2 * kOrdClasses);
+  // per cell of a pass: (estimate high word << 32 | sampled row), then its class word
+  unsigned long long *key =
+      reinterpret_cast<unsigned long long *>(reinterpret_cast<char *>(sm) + kOrdKeyOffset);
+  unsigned *ctr = reinterpret_cast<unsigned *>(a.ord_ws + kOrdClasses);
+  const int per = (a.cells + gridDim.x - 1) / gridDim.x;
+  const int c0 = min(a.cells, (int)blockIdx.x * per), c1 = min(a.cells, c0 + per);
+  const int nr = a.ord_nrows;
+  // a share of one pass keeps its class words in shared memory
+  const bool one_piece = c1 - c0 <= kOrdPiece;
+  for (int i = threadIdx.x; i < kOrdClasses; i += blockDim.x) hist[i] = 0;
+  if (threadIdx.x == 0) *bkey = 0ull;
+  for (int p0 = c0; p0 < c1; p0 += kOrdPiece) {
+    const int pc = min(kOrdPiece, c1 - p0);
+    for (int i = threadIdx.x; i < pc; i += blockDim.x) key[i] = 0ull;
+    __syncthreads();
+    // the pass's sampled diagonal entries, flattened; each thread issues a
+    // batch of independent loads before it folds them in
+    const int m = pc * nr;
+    for (int j0 = threadIdx.x; j0 < m; j0 += kOrdBatch * blockDim.x) {
+      double v[kOrdBatch];
+      int cl[kOrdBatch], q[kOrdBatch];
+#pragma unroll
+      for (int u = 0; u < kOrdBatch; ++u) {
+        const int j = j0 + u * blockDim.x;
+        cl[u] = j < m ? j / nr : -1;
+        q[u] = j - cl[u] * nr;
+        if (cl[u] >= 0)
+          v[u] = __ldg(a.A + (size_t)(p0 + cl[u]) * a.nnz + __ldg(a.ord_rows + q[u]));
+      }
+#pragma unroll
+      for (int u = 0; u < kOrdBatch; ++u)
+        if (cl[u] >= 0)
+          atomicMax(key + cl[u], (unsigned long long)diag_departure_hi(v[u]) << 32 | (unsigned)q[u]);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < pc; i += blockDim.x) {
+      const unsigned long long kk = key[i];
+      const int k = difficulty_class((unsigned)(kk >> 32));
+      const int w = k | atomicAdd(hist + k, 1) << 6;
+      if (a.ord_hits) atomicMax(bkey, kk);
+      if (one_piece) key[i] = (unsigned)w;
+      else a.ord_cls[p0 + i] = w;
+    }
+    __syncthreads();
+  }
+  // where the CTA's hardest cell peaked (the host picks the rows to sample)
+  if (a.ord_hits && threadIdx.x == 0 && c1 > c0) atomicAdd(a.ord_hits + (unsigned)*bkey, 1u);
+  for (int k = threadIdx.x; k < kOrdClasses; k += blockDim.x)
+    base[k] = hist[k] ? atomicAdd(a.ord_ws + k, hist[k]) : 0;
+  grid_barrier_bounded(ctr, gridDim.x, a.ord_err);
+  if (threadIdx.x < 32) {
+    // exclusive prefix of the class totals, two classes per lane
+    const int l = threadIdx.x;
+    const int ta = __ldcg(a.ord_ws + 2 * l), tb = __ldcg(a.ord_ws + 2 * l + 1);
+    int s = ta + tb;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int t = __shfl_up_sync(kFull, s, o);
+      if (l >= o) s += t;
+    }
+    hist[2 * l] = s - ta - tb;
+    hist[2 * l + 1] = s - tb;
+  }
+  __syncthreads();
+  for (int c = c0 + threadIdx.x; c < c1; c += blockDim.x) {
+    const int w = one_piece ? (int)key[c - c0] : __ldcg(a.ord_cls + c);
+    const int k = w & (kOrdClasses - 1);
+    const int pos = hist[k] + base[k] + (w >> 6);
+    if (pos < a.cells) __stcg(a.ord_out + pos, c + 1);  // in range unless the barrier timed out
+  }
+  __syncthreads();  // the warps' solve regions overlap the shared memory used here
+}
+
+// Wait, bounded in time as the barrier, until the in-launch ordering has
+// written order entry *p.  The entry is the only datum passed, so a relaxed
+// load suffices (an acquire would also invalidate the SM's L1 each time).
+__device__ __forceinline__ void wait_order_entry(const int *p, int *err) {
+  const long long t0 = clock64();
+  for (;;) {
+    int v;
+    asm volatile("ld.relaxed.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    if (v != 0) return;
+    if (clock64() - t0 > (1ll << 31)) {
+      if (err) {
+        *(volatile int *)err = 1;
+        __threadfence_system();
+      }
+      return;
+    }
+    __nanosleep(32);
+  }
+}
+
+
+// Next group of this warp in a launch with the dynamic queue (false when none
+// is left).  An ordered launch (a.order set) first gives every warp one group
+// of a stratified wave, or spreads the tickets over the order when there are
+// fewer groups than warps (WarpArgs::ord_wave); `first` starts true.
+template <class Args>
+__device__ __forceinline__ bool take_group(const Args &a, int warp, int lane, bool &first,
+                                           unsigned &g) {
+  const bool strat = a.order && a.ord_stride == 0 && a.ord_wave > 0;
+  if (first && strat) {
+    first = false;
+    const unsigned B = gridDim.x, b = blockIdx.x, w = (unsigned)warp;
+    g = w * B + ((w & 1u) ? B - 1u - b : b);
+    return true;
+  }
+  first = false;
+  unsigned t = 0;
+  if (lane == 0) t = atomicAdd(a.queue, 1u);
+  t = __shfl_sync(kFull, t, 0);
+  if (strat) t += (unsigned)a.ord_wave;
+  if (t >= (unsigned)a.ngroups) return false;
+  if (a.order && a.ord_stride && t < (unsigned)a.ord_wave)
+    t = (unsigned)((unsigned long long)t * (unsigned)a.ord_stride % (unsigned)a.ord_wave);
+  g = t;
+  return true;
+}
+
+// In-launch ordering: lanes 0 .. k-1 wait for the order entries of group g's
+// k cells; returns whether this lane owns one (to clear it after the solve).
+template <class Args>
+__device__ __forceinline__ bool await_order_entries(const Args &a, unsigned g, int k, int lane) {
+  if (!a.ord_ws) return false;
+  const int p = (int)g * k + lane;
+  const bool mine = lane < k && p < a.cells;
+  if (mine) wait_order_entry(a.order + p, a.ord_err);
+  __syncwarp();
+  return mine;
+}
+
+// End of a launch with the dynamic queue: the last warp to finish (every
+// other warp has taken its last group before counting itself done) resets
+// the queue pair and, after an in-launch ordering (every CTA is past its
+// barrier), the ordering's class totals and barrier counter, so both are
+// ready for the next launch in stream order.
+template <class Args>
+__device__ __forceinline__ void finish_queue(const Args &a, bool ordered, int warps_total,
+                                             int lane) {
+  if (lane != 0) return;
+  __threadfence();
+  if (atomicAdd(a.queue + 1, 1u) == (unsigned)warps_total - 1u) {
+    atomicExch(a.queue, 0u);
+    atomicExch(a.queue + 1, 0u);
+    if (ordered && a.ord_ws)
+      for (int i = 0; i < kOrdWords; ++i) atomicExch(a.ord_ws + i, 0);
+  }
+}
+
 }  // namespace camp
