@@ -211,6 +211,9 @@ camp_status camp_solver_solve_host(camp_solver_t h, int cells,
  * CAMP_CELL_MAXIT after that).  iters_out = total FP32 inner iterations,
  * sweeps_out [cells] (int32, may be NULL) = outer sweeps that ran an inner
  * solve; resid_out = final FP64 true relative residual.  Device pointers.
+ * The handle's cell ordering (camp_solver_set_ordering) applies when several
+ * cells share a warp (at most 48 species with the automatic arrangement);
+ * results do not depend on it.
  */
 camp_status camp_solver_solve_mixed(camp_solver_t h, int cells,
                                     const double *A_vals, const double *b,
