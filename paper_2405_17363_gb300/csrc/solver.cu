@@ -452,22 +452,27 @@ int spread_stride(int wave) {
 // the host-mapped time-out word, the peak-row counts (device and pinned
 // host copies), the sampled positions and the read-back event.
 cudaError_t ordering_state(camp_solver_t h) {
+  // each piece allocated once: a call after a failed one completes the rest
   cudaError_t e = cudaSuccess;
   if (!h->h_ord_err) {
     if ((e = cudaHostAlloc(&h->h_ord_err, sizeof(int), cudaHostAllocMapped)) != cudaSuccess)
       return e;
     *h->h_ord_err = 0;
-    if ((e = cudaHostGetDevicePointer(&h->d_ord_err, h->h_ord_err, 0)) != cudaSuccess) return e;
   }
-  if (h->n > kOrdSample && !h->ev_hits) {
-    if ((e = cudaMalloc(&h->d_hits, (size_t)h->n * sizeof(unsigned))) != cudaSuccess) return e;
-    if ((e = cudaMalloc(&h->d_samp, kOrdSample * sizeof(int))) != cudaSuccess) return e;
-    if ((e = cudaHostAlloc(&h->h_hits, (size_t)h->n * sizeof(unsigned), cudaHostAllocDefault)) !=
-        cudaSuccess)
-      return e;
-    if ((e = cudaEventCreateWithFlags(&h->ev_hits, cudaEventDisableTiming)) != cudaSuccess)
-      return e;
-  }
+  if (!h->d_ord_err &&
+      (e = cudaHostGetDevicePointer(&h->d_ord_err, h->h_ord_err, 0)) != cudaSuccess)
+    return e;
+  if (h->n <= kOrdSample) return cudaSuccess;  // the whole diagonal is the sample
+  if (!h->d_hits && (e = cudaMalloc(&h->d_hits, (size_t)h->n * sizeof(unsigned))) != cudaSuccess)
+    return e;
+  if (!h->d_samp && (e = cudaMalloc(&h->d_samp, kOrdSample * sizeof(int))) != cudaSuccess)
+    return e;
+  if (!h->h_hits && (e = cudaHostAlloc(&h->h_hits, (size_t)h->n * sizeof(unsigned),
+                                       cudaHostAllocDefault)) != cudaSuccess)
+    return e;
+  if (!h->ev_hits &&
+      (e = cudaEventCreateWithFlags(&h->ev_hits, cudaEventDisableTiming)) != cudaSuccess)
+    return e;
   return cudaSuccess;
 }
 
