@@ -364,14 +364,19 @@ class Solver:
         return gA
 
     def solve_mixed(self, A_vals, b, tol=1e-10, max_sweeps=20, tol_inner=1e-5,
-                    maxit_inner=50):
+                    maxit_inner=50, out=None):
+        """Returns (x, iters, sweeps, resid, status) as CUDA tensors (into
+        `out` when given)."""
         cells = b.shape[0]
         dev = b.device
-        x = torch.empty((cells, self.n), dtype=torch.float64, device=dev)
-        iters = torch.empty(cells, dtype=torch.int32, device=dev)
-        sweeps = torch.empty(cells, dtype=torch.int32, device=dev)
-        resid = torch.empty(cells, dtype=torch.float64, device=dev)
-        status = torch.empty(cells, dtype=torch.int32, device=dev)
+        if out is None:
+            x = torch.empty((cells, self.n), dtype=torch.float64, device=dev)
+            iters = torch.empty(cells, dtype=torch.int32, device=dev)
+            sweeps = torch.empty(cells, dtype=torch.int32, device=dev)
+            resid = torch.empty(cells, dtype=torch.float64, device=dev)
+            status = torch.empty(cells, dtype=torch.int32, device=dev)
+        else:
+            x, iters, sweeps, resid, status = out
         camp_solver_solve_mixed(self.h, cells, A_vals, b, x, tol, max_sweeps, tol_inner,
                                 maxit_inner, iters, sweeps, resid, status)
         return x, iters, sweeps, resid, status

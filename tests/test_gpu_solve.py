@@ -26,13 +26,19 @@ def to_dev(a, dev):
 
 def run_gpu(camp, mech, A_vals, b, tol, maxit, dev, arrangement=None, x0=None,
             transpose=False):
+    import torch
     s = camp.Solver(mech.row_ptr, mech.col_idx)
     if arrangement is not None:
         s.set_arrangement(*arrangement)
+    cells = b.shape[0]
+    # outputs poisoned (NaN, -7): a cell the launch skipped cannot pass
+    poison = (torch.full((cells, mech.n), float("nan"), dtype=torch.float64, device=dev),
+              torch.full((cells,), -7, dtype=torch.int32, device=dev),
+              torch.full((cells,), float("nan"), dtype=torch.float64, device=dev),
+              torch.full((cells,), -7, dtype=torch.int32, device=dev))
     x, it, res, st = s.solve(to_dev(A_vals, dev), to_dev(b, dev), tol, maxit,
                              x0=None if x0 is None else to_dev(x0, dev),
-                             transpose=transpose)
-    import torch
+                             transpose=transpose, out=poison)
     torch.cuda.synchronize()
     out = dict(x=x.cpu().numpy(), iters=it.cpu().numpy(), resid=res.cpu().numpy(),
                status=st.cpu().numpy())
@@ -180,6 +186,13 @@ def test_initial_guess_and_transpose(camp, cuda):
         parity.compare(mT, AT, cb.b, tol, gpu, orcT, f"T/{name}")
 
 
+def _poison(out):
+    """Fill output buffers with values no solve writes (NaN, -7), so that a
+    cell a launch skipped cannot pass for a solved one."""
+    for t in out:
+        t.fill_(float("nan") if t.is_floating_point() else -7)
+
+
 @pytest.mark.parametrize("wid", [1, 4])
 def test_difficulty_ordering_gives_identical_results(camp, cuda, wid):
     """Handing cells to warps hardest first changes which cells share a warp,
@@ -202,9 +215,11 @@ def test_difficulty_ordering_gives_identical_results(camp, cuda, wid):
         for transpose in (False, True):
             s.set_ordering(0)
             ref = [t.clone() for t in s.solve(A, b, tol, maxit, transpose=transpose)]
+            out = [torch.empty_like(t) for t in ref]
             for mode in (1, 2, 1):
                 s.set_ordering(mode)
-                got = s.solve(A, b, tol, maxit, transpose=transpose)
+                _poison(out)  # a cell the launch skipped keeps the poison
+                got = s.solve(A, b, tol, maxit, transpose=transpose, out=out)
                 torch.cuda.synchronize()
                 for r, g in zip(ref, got):
                     assert torch.equal(r, g), (cells, transpose, mode)
@@ -225,11 +240,11 @@ def test_ordering_sample_and_recalibration(camp, cuda):
     b = torch.as_tensor(cb.b, device=cuda)
     s = camp.Solver(m.row_ptr, m.col_idx)
     ref = [t.clone() for t in s.solve(A, b, tol, maxit)]
+    out = [torch.empty_like(t) for t in ref]
     s.set_ordering(1)
     for rep in range(140):
-        got = s.solve(A, b, tol, maxit, transpose=False)
-        if rep % 7 == 0:
-            torch.cuda.synchronize()
+        _poison(out)
+        got = s.solve(A, b, tol, maxit, transpose=False, out=out)
         for r, g in zip(ref, got):
             assert torch.equal(r, g), rep
     s.close()
@@ -239,9 +254,11 @@ def test_ordering_sample_and_recalibration(camp, cuda):
     b = torch.as_tensor(small.b, device=cuda)
     s = camp.Solver(mech.row_ptr, mech.col_idx)
     ref = [t.clone() for t in s.solve(A, b, tol, maxit)]
+    out = [torch.empty_like(t) for t in ref]
     s.set_ordering(1)
     for rep in range(3):
-        got = s.solve(A, b, tol, maxit)
+        _poison(out)
+        got = s.solve(A, b, tol, maxit, out=out)
         for r, g in zip(ref, got):
             assert torch.equal(r, g), rep
     s.close()
