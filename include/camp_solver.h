@@ -139,9 +139,10 @@ camp_status camp_solver_set_arrangement(camp_solver_t h, int arrangement,
  *      64th; in between only the (up to 8) rows where it peaked, picked on
  *      the host from the counts of that full read (copied back without
  *      blocking).  Device scratch: 8 bytes per cell plus 4 per row.
- *      Solves on other streams (camp_solver_solve_host's chunks) and
- *      launches whose warp regions cannot lend the ordering 2,576 bytes of
- *      shared memory use index order or mode 2.  Under stream capture the
+ *      Solves on other streams (camp_solver_solve_host's chunks) use index
+ *      order; launches whose warp regions cannot lend the ordering 2,576
+ *      bytes of shared memory, or whose cooperative launch the GPU refuses
+ *      (fewer SMs available than its occupancy query counts), use mode 2.  Under stream capture the
  *      last picked rows are used as they are (allocate first: run one solve
  *      before capturing).  Every wait of the launch is bounded (about a
  *      second); if one runs out the launch completes with invalid results

@@ -500,6 +500,46 @@ cudaError_t pick_sample(camp_solver_t h, cudaStream_t st) {
   return cudaSuccess;
 }
 
+// The separate ordering pass (a memset, a classify and a scatter launch):
+// a.order points at its result.
+template <class Args>
+camp_status separate_ordering(camp_solver_t h, Args &a, const double *A_vals, cudaStream_t st) {
+  cudaError_t e = cudaSuccess;
+  const size_t need = difficulty_scratch_bytes(a.cells);
+  if (need > h->order_cap) {
+    cudaFree(h->d_order_scratch);
+    h->d_order_scratch = nullptr;
+    h->order_cap = 0;
+    if ((e = cudaMalloc(&h->d_order_scratch, need)) != cudaSuccess)
+      return fail(CAMP_ENOMEM, "ordering scratch: %s", cudaGetErrorString(e));
+    h->order_cap = need;
+  }
+  int *order = nullptr;
+  e = launch_difficulty_order(A_vals, a.cells, h->fwd.n, h->fwd.nnz, h->fwd.d_diag,
+                              h->d_order_scratch, &order, st);
+  if (e != cudaSuccess) return cuda_fail(e, "difficulty ordering");
+  a.order = order;
+  return CAMP_OK;
+}
+
+// A cooperative launch was refused as too large (the GPU offers fewer SMs
+// than the occupancy query assumed, e.g. a partitioned GPU): order by the
+// separate pass instead and clear the in-launch fields.  The refused launch
+// ran nothing, so the order entries and the workspace are still zero.
+template <class Args>
+camp_status fall_back_to_separate_ordering(camp_solver_t h, Args &a, const double *A_vals,
+                                           cudaStream_t st) {
+  (void)cudaGetLastError();
+  a.ord_out = nullptr;
+  a.ord_ws = nullptr;
+  a.ord_cls = nullptr;
+  a.ord_rows = nullptr;
+  a.ord_nrows = 0;
+  a.ord_hits = nullptr;
+  a.ord_err = nullptr;
+  return separate_ordering(h, a, A_vals, st);
+}
+
 // Difficulty ordering of a warp-packed solve on the handle's own stream (one
 // workspace per handle).  Ordering 1 runs inside the (cooperative) solve
 // launch, borrowing kOrdSmemBytes of the warp regions (smem_free bytes of
@@ -526,23 +566,7 @@ camp_status setup_ordering(camp_solver_t h, Args &a, const double *A_vals, size_
       return cuda_fail(e, "ordering scratch");
     h->ord_cap = (size_t)cells;
   }
-  const size_t need = difficulty_scratch_bytes(cells);
-  if (!inl && need > h->order_cap) {
-    cudaFree(h->d_order_scratch);
-    h->d_order_scratch = nullptr;
-    h->order_cap = 0;
-    if ((e = cudaMalloc(&h->d_order_scratch, need)) != cudaSuccess)
-      return fail(CAMP_ENOMEM, "ordering scratch: %s", cudaGetErrorString(e));
-    h->order_cap = need;
-  }
-  if (!inl) {
-    int *order = nullptr;
-    e = launch_difficulty_order(A_vals, cells, h->fwd.n, h->fwd.nnz, h->fwd.d_diag,
-                                h->d_order_scratch, &order, st);
-    if (e != cudaSuccess) return cuda_fail(e, "difficulty ordering");
-    a.order = order;
-    return CAMP_OK;
-  }
+  if (!inl) return separate_ordering(h, a, A_vals, st);
   if ((e = ordering_state(h)) != cudaSuccess) return cuda_fail(e, "ordering state");
   a.ord_out = h->d_ord;
   a.ord_cls = h->d_ord + h->ord_cap;
@@ -679,6 +703,12 @@ camp_status do_solve(camp_solver_t h, int cells, const double *A_vals,
     const int grid = std::max(1, std::min(need, h->sms * occ));
     set_wave(a, grid, wpb);
     e = launch_warp(E, a, wpb, grid, smem, st);
+    if (e == cudaErrorCooperativeLaunchTooLarge && a.ord_ws) {
+      const camp_status rs = fall_back_to_separate_ordering(h, a, A_vals, st);
+      if (rs != CAMP_OK) return rs;
+      calibrate = false;
+      e = launch_warp(E, a, wpb, grid, smem, st);
+    }
     if (e != cudaSuccess) return cuda_fail(e, "warp kernel launch");
     return calibrate ? read_back_hits(h, st) : CAMP_OK;
   }
@@ -1336,8 +1366,14 @@ camp_status camp_solver_solve_mixed(camp_solver_t h, int cells,
   const int need = (a.ngroups + wpb - 1) / wpb;
   const int grid = std::max(1, std::min(need, h->sms * occ));
   set_wave(a, grid, wpb);
-  if ((e = launch_mixed(E, a, wpb, grid, smem, h->stream)) != cudaSuccess)
-    return cuda_fail(e, "mixed kernel launch");
+  e = launch_mixed(E, a, wpb, grid, smem, h->stream);
+  if (e == cudaErrorCooperativeLaunchTooLarge && a.ord_ws) {
+    const camp_status rs = fall_back_to_separate_ordering(h, a, A_vals, h->stream);
+    if (rs != CAMP_OK) return rs;
+    calibrate = false;
+    e = launch_mixed(E, a, wpb, grid, smem, h->stream);
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "mixed kernel launch");
   return calibrate ? read_back_hits(h, h->stream) : CAMP_OK;
 }
 
