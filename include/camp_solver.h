@@ -20,12 +20,14 @@
  *  - Ownership.  Array arguments are device pointers owned by the caller
  *    (except camp_solver_solve_host, which takes host pointers).  The solver
  *    handle owns only its device copies of the pattern, the transposed
- *    pattern, the SpMV schedules and its staging buffers.
+ *    pattern, the SpMV schedules, its staging buffers and the cell-ordering
+ *    workspace.
  *  - Streams.  Work is enqueued on the stream set with camp_solver_set_stream
  *    (default: the legacy default stream) and returns without waiting.  The
- *    solves of one handle share its device work queue: calls on one handle
- *    must not overlap on the GPU (keep them on one stream, or use one handle
- *    per stream); different handles are independent.
+ *    solves of one handle share its device work queue and ordering state:
+ *    calls on one handle must not overlap on the GPU or come from two host
+ *    threads at once (keep them on one stream and one thread, or use one
+ *    handle per stream); different handles are independent.
  *  - Errors.  A negative camp_status means nothing was enqueued (argument or
  *    pattern error) or the CUDA runtime reported an error; camp_last_error()
  *    gives a message.  Non-convergence of a cell is NOT an error: it shows in
