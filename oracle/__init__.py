@@ -52,7 +52,7 @@ def _load():
             lib.orc_bicgstab_cell.argtypes = [I, P, P, P, P, D, I, I, P, P, P]
             lib.orc_bicgstab_batch.restype = I
             lib.orc_bicgstab_batch.argtypes = [I, I, I, P, P, P, P, D, I, I, P, P,
-                                               P, P, I]
+                                               P, P, P, I]
             lib.orc_mixed_batch.restype = I
             lib.orc_mixed_batch.argtypes = [I, I, I, P, P, P, P, D, I, D, I, P, P,
                                             P, P, P, I]
@@ -86,7 +86,8 @@ def solve(row_ptr, col_idx, A_vals, b, tol=1e-10, maxit=500, x0=None,
           threads=1):
     """Solve every cell.  A_vals [cells, nnz], b [cells, n] (FP64).
 
-    Returns dict(x, iters, resid, status, threads)."""
+    Returns dict(x, iters, resid, status, restarts, threads); restarts counts
+    each cell's restarts from r = b - A x (residual replacement or breakdown)."""
     lib = _load()
     rp, ci = _i32(row_ptr), _i32(col_idx)
     A, B = _f64(np.atleast_2d(A_vals)), _f64(np.atleast_2d(b))
@@ -98,11 +99,13 @@ def solve(row_ptr, col_idx, A_vals, b, tol=1e-10, maxit=500, x0=None,
     iters = np.zeros(cells, dtype=np.int32)
     resid = np.zeros(cells)
     status = np.zeros(cells, dtype=np.int32)
+    restarts = np.zeros(cells, dtype=np.int32)
     used = lib.orc_bicgstab_batch(cells, n, nnz, _p(rp), _p(ci), _p(A), _p(B),
                                   float(tol), int(maxit), int(x0 is not None),
                                   _p(x), _p(iters), _p(resid), _p(status),
-                                  int(threads))
-    return dict(x=x, iters=iters, resid=resid, status=status, threads=used)
+                                  _p(restarts), int(threads))
+    return dict(x=x, iters=iters, resid=resid, status=status, restarts=restarts,
+                threads=used)
 
 
 def solve_mixed(row_ptr, col_idx, A_vals, b, tol=1e-10, max_sweeps=20,

@@ -74,16 +74,19 @@ static double dot(int n, const double *u, const double *w) {
 
 /*
  * One cell.  x holds the initial guess on entry when x0_given != 0; x is the
- * solution on return.  Returns the status code.
+ * solution on return.  Returns the status code.  restarts_out (or NULL)
+ * receives the number of restarts from r = b - A x (residual replacement
+ * after a failed true-residual test, or after a breakdown).
  */
-int orc_bicgstab_cell(int n, const int *rp, const int *ci, const double *a,
-                      const double *b, double tol, int maxit, int x0_given,
-                      double *x, int *iters_out, double *resid_out) {
+int orc_bicgstab_cell_r(int n, const int *rp, const int *ci, const double *a,
+                        const double *b, double tol, int maxit, int x0_given,
+                        double *x, int *iters_out, double *resid_out,
+                        int *restarts_out) {
   /* the nine work arrays */
   double *work = (double *)malloc(sizeof(double) * 9 * (size_t)(n > 0 ? n : 1));
   double *r = work, *rh = r + n, *p = rh + n, *v = p + n, *s = v + n,
          *t = s + n, *ph = t + n, *sh = ph + n, *dinv = sh + n;
-  int status = ORC_MAXIT, iters = 0;
+  int status = ORC_MAXIT, iters = 0, restarts = 0;
   double resid = 0.0;
 
   /* Jacobi preconditioner M = diag(A), applied on the right */
@@ -172,12 +175,21 @@ int orc_bicgstab_cell(int n, const int *rp, const int *ci, const double *a,
     if (broke && ++nbreak >= 2) { status = ORC_BREAKDOWN; break; }
     (void)conv;
     for (int i = 0; i < n; ++i) r[i] = t[i]; /* residual replacement */
+    ++restarts;
   }
 done:
   *iters_out = iters;
   *resid_out = resid;
+  if (restarts_out) *restarts_out = restarts;
   free(work);
   return status;
+}
+
+int orc_bicgstab_cell(int n, const int *rp, const int *ci, const double *a,
+                      const double *b, double tol, int maxit, int x0_given,
+                      double *x, int *iters_out, double *resid_out) {
+  return orc_bicgstab_cell_r(n, rp, ci, a, b, tol, maxit, x0_given, x, iters_out,
+                             resid_out, NULL);
 }
 
 /* ---- FP32 inner solve for the mixed-precision refinement ---------------- */
@@ -337,7 +349,7 @@ typedef struct {
   double tol, tol_in;
   int maxit, maxit_in, max_sweeps, x0_given;
   double *x, *resid;
-  int *iters, *status, *sweeps;
+  int *iters, *status, *sweeps, *restarts;
   int next; /* shared cell counter */
 } batch_t;
 
@@ -350,9 +362,10 @@ static void *batch_worker(void *arg) {
     const double *b = B->b + (size_t)c * B->n;
     double *x = B->x + (size_t)c * B->n;
     if (B->kind == 0) {
-      B->status[c] = orc_bicgstab_cell(B->n, B->rp, B->ci, a, b, B->tol,
-                                       B->maxit, B->x0_given, x, &B->iters[c],
-                                       &B->resid[c]);
+      B->status[c] = orc_bicgstab_cell_r(B->n, B->rp, B->ci, a, b, B->tol,
+                                         B->maxit, B->x0_given, x, &B->iters[c],
+                                         &B->resid[c],
+                                         B->restarts ? &B->restarts[c] : NULL);
     } else {
       int sw = 0;
       B->status[c] = orc_mixed_cell(B->n, B->rp, B->ci, a, b, B->tol,
@@ -384,16 +397,18 @@ static int run_batch(batch_t *B, int nthreads) {
 }
 
 /* All cells of a batch: a [cells x nnz], b/x [cells x n]; cells are claimed
- * from a shared counter by nthreads threads.  Returns the threads used. */
+ * from a shared counter by nthreads threads.  restarts [cells] (or NULL)
+ * receives each cell's restart count.  Returns the threads used. */
 int orc_bicgstab_batch(int cells, int n, int nnz, const int *rp, const int *ci,
                        const double *a, const double *b, double tol, int maxit,
                        int x0_given, double *x, int *iters, double *resid,
-                       int *status, int nthreads) {
+                       int *status, int *restarts, int nthreads) {
   batch_t B;
   memset(&B, 0, sizeof B);
   B.kind = 0; B.cells = cells; B.n = n; B.nnz = nnz; B.rp = rp; B.ci = ci;
   B.a = a; B.b = b; B.tol = tol; B.maxit = maxit; B.x0_given = x0_given;
   B.x = x; B.iters = iters; B.resid = resid; B.status = status;
+  B.restarts = restarts;
   int used = run_batch(&B, nthreads);
   return used > 0 ? used : 1;
 }

@@ -97,10 +97,12 @@ class Mechanism:
         return A
 
 
-def make_mechanism(n: int, R: int, seed: int) -> Mechanism:
+def make_mechanism(n: int, R: int, seed: int,
+                   log10_k: tuple[float, float] = (-6.0, 2.0)) -> Mechanism:
     """Draw a mechanism.  Draw order: for r = 0..R-1 the species of reaction r
     (``rng.choice(n, 2 or 3, replace=False)``: reactant(s) first, product last),
-    then all ``R`` log10 rate constants ``rng.uniform(-6, 2, R)``."""
+    then all ``R`` log10 rate constants ``rng.uniform(*log10_k, R)`` (by
+    default rate constants in [1e-6, 1e2])."""
     if n < 3:
         raise ValueError("a bimolecular A+B->C reaction needs n >= 3 species")
     rng = np.random.default_rng(seed)
@@ -116,7 +118,7 @@ def make_mechanism(n: int, R: int, seed: int) -> Mechanism:
             a, b, c = rng.choice(n, 3, replace=False)
             reactants[r] = (a, b)
             products[r] = c
-    k = 10.0 ** rng.uniform(-6.0, 2.0, R)
+    k = 10.0 ** rng.uniform(log10_k[0], log10_k[1], R)
 
     # (row, col, reaction, species multiplying k or -1, sign)
     contrib = []
@@ -188,8 +190,10 @@ def make_cells(mech: Mechanism, cells: int, seed: int,
                      b=np.ascontiguousarray(b))
 
 
-# Workloads: (name, [(n, R, cells, gamma)], tol, maxit).  Mechanism seed 1000+id
-# (+10 per extra mechanism), cell seed 2000+id (+10 per extra mechanism).
+# Workloads: (name, [(n, R, cells, gamma[, options])], tol, maxit).  Mechanism
+# seed 1000+id (+10 per extra mechanism), cell seed 2000+id (+10 per extra
+# mechanism).  Options: "log10_k" (rate-constant exponent range, default
+# (-6, 2)) and "conc" (concentration range, default (1e-12, 1e-3)).
 WORKLOADS = {
     0: ("30 species / 60 reactions, 64 cells, gamma 1e-2",
         [(30, 60, 64, 1e-2)], 1e-10, 200),
@@ -202,6 +206,13 @@ WORKLOADS = {
         [(80, 200, 10000, (1e-4, 1e-1))], 1e-10, 500),
     4: ("mixed precision: 150 species / 400 reactions, 100000 cells, gamma logU[1e-4,1e-1]",
         [(150, 400, 100000, (1e-4, 1e-1))], 1e-10, 500),
+    # Hard regime (parity only): stiffer and more strongly coupled systems
+    # (rate constants up to 1e4, gamma up to 10, concentrations up to 1), so
+    # that Jacobi-BiCGSTAB needs tens to hundreds of iterations per cell.
+    5: ("hard: 80 species / 200 reactions, 10000 cells, k logU[1e-4,1e4], "
+        "gamma logU[1e-2,10], conc logU[1e-3,1]",
+        [(80, 200, 10000, (1e-2, 10.0), {"log10_k": (-4.0, 4.0), "conc": (1e-3, 1.0)})],
+        1e-10, 500),
 }
 
 
@@ -211,8 +222,12 @@ def workload(wid: int, cells: int | None = None):
     Returns (list[CellBatch], tol, maxit)."""
     _, mechs, tol, maxit = WORKLOADS[wid]
     out = []
-    for j, (n, R, C, g) in enumerate(mechs):
-        mech = make_mechanism(n, R, 1000 + wid + 10 * j)
+    for j, spec in enumerate(mechs):
+        n, R, C, g = spec[:4]
+        opt = spec[4] if len(spec) > 4 else {}
+        mech = make_mechanism(n, R, 1000 + wid + 10 * j,
+                              log10_k=opt.get("log10_k", (-6.0, 2.0)))
         out.append(make_cells(mech, C if cells is None else cells,
-                              2000 + wid + 10 * j, gamma=g))
+                              2000 + wid + 10 * j, gamma=g,
+                              conc_range=opt.get("conc", (1e-12, 1e-3))))
     return out, tol, maxit

@@ -100,13 +100,17 @@ def test_solve_host_equals_device(cuda, cells, pinned_out):
     s.close()
 
 
-def test_adjoint_full_size_sampled(cuda):
+def test_adjoint_full_size_all_cells(cuda):
     """Adjoint workload at full size (80 species, 10000 cells, tol 1e-10): the
-    gradients of L = sum_c w_c . x_c from the autograd Function on 16 sampled
+    gradients of L = sum_c w_c . x_c from the autograd Function, every cell
+    against the oracle's adjoint (x, lambda = dL/db and dL/dA_vals each within
+    the 1e-8 bar, no cell needing a conditioning fallback), and 16 sampled
     cells against dense LAPACK gradients and central differences (step 1e-6,
     dense forward solves)."""
+    import os
     import torch
     from paper_2405_17363_gb300 import camp
+    from tests import parity
     cbs, tol, maxit = synth.workload(3)
     cb = cbs[0]
     m = cb.mech
@@ -117,8 +121,28 @@ def test_adjoint_full_size_sampled(cuda):
     x, it, res, st = camp.solve(A, b, s, tol, maxit)
     (x * torch.as_tensor(w, device=cuda)).sum().backward()
     assert int((st == 0).sum()) == cb.cells
+    X = x.detach().cpu().numpy()
     gA = A.grad.cpu().numpy()
     gb = b.grad.cpu().numpy()
+    threads = os.cpu_count() or 8
+    fwd = oracle.solve(m.row_ptr, m.col_idx, cb.A_vals, cb.b, tol, maxit, threads=threads)
+    adj = oracle.adjoint(m.row_ptr, m.col_idx, cb.A_vals, fwd["x"], w, tol=tol, maxit=maxit,
+                         threads=threads)
+    assert np.all(adj["status"] == 0)
+    e_x = parity.rel_err(X, fwd["x"])
+    e_l = parity.rel_err(gb, adj["gb"])
+    e_g = parity.rel_err(gA, adj["gA"])
+    assert e_x.max() <= parity.REL_TOL, e_x.max()
+    assert e_l.max() <= parity.REL_TOL, e_l.max()
+    # gA = -lambda[row] x[col] on the pattern: ||d gA|| <= ||d lambda|| ||x_gpu||
+    # + ||lambda|| ||d x||, so relative to ||gA|| the error is bounded by the
+    # two relative errors times q = ||lambda|| ||x|| / ||gA||
+    q = (np.linalg.norm(adj["gb"], axis=1) * np.linalg.norm(fwd["x"], axis=1)
+         / np.linalg.norm(adj["gA"], axis=1))
+    bound = (e_l * (1 + e_x) + e_x) * q * (1 + 1e-6) + 1e-14
+    assert np.all(e_g <= bound), np.max(e_g / bound)
+    print(f"adjoint 80 sp x 10000 cells: max error x {e_x.max():.2e}, lambda {e_l.max():.2e}, "
+          f"gA {e_g.max():.2e}")
     rows = np.repeat(np.arange(m.n), np.diff(m.row_ptr))
     rng = np.random.default_rng(16)
     for c in rng.choice(cb.cells, 16, replace=False):

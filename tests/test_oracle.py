@@ -384,6 +384,7 @@ def test_residual_replacement_matches_scipy_restart():
             checked += 1
             assert out["status"][c] == oracle.CONVERGED
             assert out["iters"][c] == it1 + it2, (c, out["iters"][c], it1, it2)
+            assert out["restarts"][c] == 1
     assert checked >= 1
 
 
@@ -480,3 +481,79 @@ def test_newton_root_satisfies_the_step_equation():
         assert np.linalg.norm(G) <= 1e-10 * np.linalg.norm(a[c])
         sol = optimize.root(lambda z: z - cb.gamma[c] * m.rates(z) - a[c], a[c], tol=1e-15)
         np.testing.assert_allclose(y, sol.x, rtol=1e-8, atol=1e-12 * np.abs(a[c]).max())
+
+
+def test_restart_count_is_zero_without_replacement():
+    """Cells that converge on their first run (true residual within tol at
+    the first exit) report no restart; SciPy needs one call for them."""
+    scipy_sparse = pytest.importorskip("scipy.sparse")
+    cbs, tol, maxit = synth.workload(1, cells=40)
+    cb = cbs[0]
+    m = cb.mech
+    out = oracle.solve(m.row_ptr, m.col_idx, cb.A_vals, cb.b, tol, maxit)
+    for c in range(cb.cells):
+        A = scipy_sparse.csr_matrix((cb.A_vals[c], m.col_idx, m.row_ptr), shape=(m.n, m.n))
+        it1, x1, info1 = _scipy_count(A, cb.b[c], tol, maxit)
+        r1 = np.linalg.norm(cb.b[c] - A @ x1) / np.linalg.norm(cb.b[c])
+        if info1 == 0 and r1 <= 0.5 * tol:
+            assert out["restarts"][c] == 0
+
+
+def test_hard_regime_is_sensitive_to_rounding():
+    """The reading behind the hard-regime parity bar: on stiff, strongly
+    coupled systems (the hard workload) the oracle itself, given right-hand
+    sides one rounding away, takes iteration counts more than two apart on
+    many cells while every converged solution stays within the 1e-8 bar; on
+    the benchmark's systems the counts do not move."""
+    from tests import parity
+    cbs, tol, maxit = synth.workload(5, cells=2000)
+    cb = cbs[0]
+    m = cb.mech
+    o = oracle.solve(m.row_ptr, m.col_idx, cb.A_vals, cb.b, tol, maxit, threads=8)
+    p = oracle.solve(m.row_ptr, m.col_idx, cb.A_vals, parity.perturbed_rhs(cb.b, 1), tol,
+                     maxit, threads=8)
+    assert o["iters"].mean() >= 30 and o["iters"].max() >= 150
+    sp = parity.spread(o, p)
+    assert sp["frac_iters_off"] >= 0.05 and sp["max_iters_off"] >= 20
+    assert np.all(o["status"] == 0) and np.all(p["status"] == 0)
+    assert parity.rel_err(p["x"], o["x"]).max() <= parity.REL_TOL
+    cbs, tol, maxit = synth.workload(1, cells=2000)
+    cb = cbs[0]
+    m = cb.mech
+    o = oracle.solve(m.row_ptr, m.col_idx, cb.A_vals, cb.b, tol, maxit, threads=8)
+    p = oracle.solve(m.row_ptr, m.col_idx, cb.A_vals, parity.perturbed_rhs(cb.b, 1), tol,
+                     maxit, threads=8)
+    assert parity.spread(o, p)["max_iters_off"] <= 1
+
+
+def test_sensitive_bar_accepts_rounding_and_rejects_planted_mistakes():
+    """compare_sensitive accepts the oracle on a third one-rounding change of
+    b (a correct implementation with different rounding) and rejects: counts
+    raised by three, a right-hand side off by 1e-6 (x misses the 1e-8 bar),
+    the oracle run to a looser tolerance (converged residuals above tol), and
+    an implementation that gives up early (a lower iteration cap)."""
+    from tests import parity
+    cbs, tol, maxit = synth.workload(5, cells=2000)
+    cb = cbs[0]
+    m = cb.mech
+
+    def run(b, t=tol):
+        return oracle.solve(m.row_ptr, m.col_idx, cb.A_vals, b, t, maxit, threads=8)
+
+    o = run(cb.b)
+    pert = [run(parity.perturbed_rhs(cb.b, s)) for s in (1, 2)]
+    ok = run(parity.perturbed_rhs(cb.b, 3))
+    parity.compare_sensitive(m, cb.A_vals, cb.b, tol, maxit, ok, o, pert, "third perturbation")
+    shifted = dict(ok, iters=np.minimum(ok["iters"] + 3, maxit))
+    with pytest.raises(AssertionError):
+        parity.compare_sensitive(m, cb.A_vals, cb.b, tol, maxit,
+                                 oracle.solve(m.row_ptr, m.col_idx, cb.A_vals, cb.b, tol, 60,
+                                              threads=8), o, pert, "early cap")
+    with pytest.raises(AssertionError):
+        parity.compare_sensitive(m, cb.A_vals, cb.b, tol, maxit, shifted, o, pert, "shift")
+    with pytest.raises(AssertionError):
+        parity.compare_sensitive(m, cb.A_vals, cb.b, tol, maxit, run(cb.b * (1 + 1e-6)), o,
+                                 pert, "wrong b")
+    with pytest.raises(AssertionError):
+        parity.compare_sensitive(m, cb.A_vals, cb.b, tol, maxit, run(cb.b, 1e-6), o, pert,
+                                 "loose tol")
