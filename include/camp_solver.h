@@ -64,7 +64,11 @@ enum {
   CAMP_CELL_CONVERGED = 0,
   CAMP_CELL_MAXIT = 1,
   CAMP_CELL_BREAKDOWN = 2,
-  CAMP_CELL_NONFINITE = 3
+  CAMP_CELL_NONFINITE = 3,
+  /* the launch that solved this cell was ordered in-launch and one of its
+   * bounded waits ran out (camp_solver_set_ordering): x and iters are not
+   * valid, resid is NaN; solve again */
+  CAMP_CELL_INVALID = 4
 };
 
 /* flags for camp_solver_solve_ex */
@@ -84,7 +88,7 @@ enum {
 /*
  * Create a solver for one sparsity pattern (the pattern shared by all cells,
  * Sec. 3.1).  row_ptr [n+1] and col_idx [nnz] are HOST arrays, copied.
- * Requirements: 1 <= n <= 4096, n <= nnz <= 65535, row_ptr[0] = 0,
+ * Requirements: 1 <= n <= 1024, n <= nnz <= 65535, row_ptr[0] = 0,
  * row_ptr[n] = nnz, nondecreasing; columns in [0, n) strictly increasing
  * within a row; every diagonal entry present.  Otherwise CAMP_EPATTERN (or
  * CAMP_EINVAL for null pointers / sizes).  Allocates device memory on the
@@ -147,12 +151,26 @@ camp_status camp_solver_set_arrangement(camp_solver_t h, int arrangement,
  *      (fewer SMs available than its occupancy query counts), use mode 2.  Under stream capture the
  *      last picked rows are used as they are (allocate first: run one solve
  *      before capturing).  Every wait of the launch is bounded (about a
- *      second); if one runs out the launch completes with invalid results
- *      and the handle's next solve call returns CAMP_ECUDA.
+ *      second).  If one runs out, the same launch marks every cell of the
+ *      call CAMP_CELL_INVALID (when status_out is given) with resid NaN,
+ *      and leaves the handle's ordering state clean, so the next call runs
+ *      normally; camp_solver_get_fault reports it without synchronising.
  *   2: a separate classify and scatter pass (a memset and two small
  *      launches before the solve; about 5 bytes of scratch per cell).
  */
 camp_status camp_solver_set_ordering(camp_solver_t h, int ordering);
+
+/*
+ * Whether a bounded wait of an in-launch ordering (ordering mode 1, the
+ * plain FP64 solve and the FP32-inner refinement) ran out in any launch of
+ * this handle since the previous query: *ordering_timed_out = 1 (and the
+ * report is cleared) or 0.  Reads a host-mapped word the GPU sets; it does
+ * not synchronise, so it covers only launches that have completed (call it
+ * after the stream has been synchronised, as one does before reading the
+ * results).  The cells of such a launch carry CAMP_CELL_INVALID.
+ * CAMP_EINVAL for a null argument.
+ */
+camp_status camp_solver_get_fault(camp_solver_t h, int *ordering_timed_out);
 
 /*
  * Solve all cells: A_vals [cells x nnz], b [cells x n] in; x [cells x n],
@@ -286,8 +304,17 @@ camp_status camp_batch_solve(camp_batch_t b, const int *cells,
  *    work overlaps on the GPU -- on different streams, or from different host
  *    threads -- race on it: order them on one stream.
  *  - Work is enqueued on `stream` (a cudaStream_t, NULL = legacy default
- *    stream): two host-to-device copies of the schedule from host memory,
- *    then the kernel.
+ *    stream): four host-to-device copies from host buffers inside the
+ *    library (the diagonal slots, the first padding slot of every lane, the
+ *    slot of every entry and the slot words), then the kernel.  The copies
+ *    read pageable host memory, so a call may wait on the host until earlier
+ *    work on the stream has finished.
+ *  - While `stream` is capturing a CUDA graph the call returns
+ *    CAMP_EUNSUPPORTED and enqueues nothing: a captured copy would read the
+ *    library's host buffers when the graph is replayed, after later calls
+ *    may have overwritten them.
+ *  - The set-up's device address is kept until the process exits: after a
+ *    cudaDeviceReset of a device, do not call this entry point on it again.
  */
 camp_status camp_solve_noalloc(int n, int nnz, const int *row_ptr,
                                const int *col_idx, int cells,

@@ -26,6 +26,7 @@ CAMP_OK, CAMP_EINVAL, CAMP_ECUDA, CAMP_ENOMEM, CAMP_EPATTERN, CAMP_EUNSUPPORTED 
     0, -1, -2, -3, -4, -5
 CAMP_CELL_CONVERGED, CAMP_CELL_MAXIT, CAMP_CELL_BREAKDOWN, CAMP_CELL_NONFINITE = \
     0, 1, 2, 3
+CAMP_CELL_INVALID = 4
 CAMP_TRANSPOSE, CAMP_X0_GIVEN = 1, 2
 CAMP_ARR_AUTO, CAMP_ARR_WARP, CAMP_ARR_BLOCK, CAMP_ARR_BLOCK_COUPLED = 0, 1, 2, 3
 
@@ -46,6 +47,8 @@ _destroy = _sig("camp_solver_destroy", [_P])
 _set_stream = _sig("camp_solver_set_stream", [_P, _P])
 _set_arr = _sig("camp_solver_set_arrangement", [_P, _I, _I, _I, _I])
 _set_ordering = _sig("camp_solver_set_ordering", [_P, _I])
+_get_fault = _sig("camp_solver_get_fault", [_P, ctypes.POINTER(_I)])
+_set_test_hooks = _sig("camp_solver_set_test_hooks", [_P, ctypes.c_longlong, _I])
 _solve = _sig("camp_solver_solve", [_P, _I, _P, _P, _P, _D, _I, _P, _P])
 _solve_ex = _sig("camp_solver_solve_ex", [_P, _I, _P, _P, _P, _D, _I, _P, _P, _P, _I])
 _grad_A = _sig("camp_solver_grad_A", [_P, _I, _P, _P, _P])
@@ -144,6 +147,23 @@ def camp_solver_set_arrangement(h: int, arrangement: int, lanes_per_cell: int = 
 
 def camp_solver_set_ordering(h: int, ordering: int):
     _check(_set_ordering(h, int(ordering)), "camp_solver_set_ordering")
+
+
+def camp_solver_get_fault(h: int) -> bool:
+    """Whether an in-launch ordering wait of this handle ran out since the
+    last query (no synchronisation; see include/camp_solver.h)."""
+    v = _I(0)
+    _check(_get_fault(h, ctypes.byref(v)), "camp_solver_get_fault")
+    return bool(v.value)
+
+
+def camp_solver_set_test_hooks(h: int, ordering_wait_cycles: int = 0,
+                               refuse_cooperative: bool = False):
+    """Test hooks (include/camp_testing.h): the ordering's wait limit in SM
+    cycles (0: default) and a switch that treats cooperative launches as
+    refused."""
+    _check(_set_test_hooks(h, int(ordering_wait_cycles), int(bool(refuse_cooperative))),
+           "camp_solver_set_test_hooks")
 
 
 def camp_solver_solve(h, cells, A_vals, b, x, tol, maxit, iters_out, resid_out):
@@ -301,6 +321,12 @@ class Solver:
 
     def set_ordering(self, ordering: int):
         camp_solver_set_ordering(self.h, ordering)
+
+    def get_fault(self) -> bool:
+        return camp_solver_get_fault(self.h)
+
+    def set_test_hooks(self, ordering_wait_cycles: int = 0, refuse_cooperative: bool = False):
+        camp_solver_set_test_hooks(self.h, ordering_wait_cycles, refuse_cooperative)
 
     def solve(self, A_vals, b, tol=1e-10, maxit=500, x0=None, transpose=False,
               out=None):

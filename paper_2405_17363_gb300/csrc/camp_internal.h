@@ -68,11 +68,14 @@ struct WarpArgs {
   // positions ord_rows[0 .. ord_nrows) (the whole diagonal, or the rows where
   // the estimate peaked before), then, through two grid barriers, writes the
   // hardest-first order to ord_out (= order) before any warp solves.
-  // ord_ws: kOrdWords ints (class totals, then the barrier counter), zero on
-  // entry and cleared by the launch's last warp; ord_cls: [cells] class |
-  // rank << 6 words; ord_hits (or null): per sampled row, the CTAs whose
-  // hardest cell peaked there; ord_err: a host-mapped word set to 1 if a
-  // barrier wait ran out of time (the launch's results are then invalid).
+  // ord_ws: kOrdWords ints (class totals, the barrier counter, the
+  // time-out flag), zero on entry and cleared by the launch's last warp;
+  // ord_cls: [cells] class | rank << 6 words; ord_hits (or null): per
+  // sampled row, the CTAs whose hardest cell peaked there; ord_err: a
+  // host-mapped word set to 1 (and left set for the host to read) when a
+  // bounded wait ran out; ord_wait: the limit of every wait, in SM clock
+  // cycles.  After a time-out the launch's last warp marks every cell of the
+  // launch CAMP_CELL_INVALID (resid NaN) and clears the order entries.
   int *ord_out;
   int *ord_ws;
   int *ord_cls;
@@ -80,6 +83,7 @@ struct WarpArgs {
   int ord_nrows;
   unsigned *ord_hits;
   int *ord_err;
+  long long ord_wait;
   // Fused assembly (assemble_bicgstab_kernel only): the cell's matrix is
   // built in shared memory as A = I - gamma J(conc) instead of read from A.
   // Lane sl runs tcount terms p: J[slot (tmeta >> 11) * Lc + sl] +=
@@ -178,9 +182,14 @@ cudaError_t launch_difficulty_order(const double *A, int cells, int n, int nnz,
 constexpr int kMaxE = 16;  // rows per lane supported by the warp kernel
 
 // Difficulty classes of the ordering (half octaves of max_i |A_ii - 1|) and
-// the in-launch ordering's workspace: class totals and one barrier counter.
+// the in-launch ordering's workspace: class totals, one barrier counter
+// (word kOrdClasses) and one time-out flag (word kOrdFlag).
 constexpr int kOrdClasses = 64;
-constexpr int kOrdWords = kOrdClasses + 1;
+constexpr int kOrdFlag = kOrdClasses + 1;
+constexpr int kOrdWords = kOrdClasses + 2;
+// Default limit of the in-launch ordering's waits (SM clock cycles, about a
+// second at 2 GHz; a legitimate wait is microseconds).
+constexpr long long kOrdWaitCycles = 1ll << 31;
 // Cells one CTA classifies per pass of the in-launch ordering, and the
 // shared-memory bytes that ordering borrows from the CTA's warp regions
 // before they are used: histogram, class bases, the CTA's hardest key, and
@@ -242,6 +251,7 @@ struct MixedArgs {
   int ord_nrows;
   unsigned *ord_hits;
   int *ord_err;
+  long long ord_wait;
 };
 // a cooperative launch when a.ord_ws is set (grid at most SMs x occupancy)
 cudaError_t launch_mixed(int E, const MixedArgs &a, int warps_per_block,

@@ -12,6 +12,7 @@
 #include <vector>
 
 #include "camp_internal.h"
+#include "camp_testing.h"
 
 namespace camp {
 cudaError_t launch_warp_1(const WarpArgs &, int, int, size_t, cudaStream_t);
@@ -339,6 +340,10 @@ struct camp_solver {
   cudaEvent_t ev_hits = nullptr;
   bool hits_pending = false;
   unsigned ordered_solves = 0;
+  // limit of the in-launch ordering's waits (SM cycles) and, for tests, a
+  // switch that treats every cooperative launch as refused
+  long long ord_wait = kOrdWaitCycles;
+  int refuse_cooperative = 0;
 };
 
 namespace {
@@ -572,6 +577,7 @@ camp_status setup_ordering(camp_solver_t h, Args &a, const double *A_vals, size_
   a.ord_cls = h->d_ord + h->ord_cap;
   a.ord_ws = (int *)(h->d_queue + 2 * (1 + kHostSolveStreams));
   a.ord_err = h->d_ord_err;
+  a.ord_wait = h->ord_wait;
   a.order = a.ord_out;
   // the diagonal is the same in both orientations: forward positions
   a.ord_rows = h->fwd.d_diag;
@@ -622,17 +628,12 @@ void set_wave(Args &a, int grid, int wpb) {
   }
 }
 
-// A bounded wait of an earlier in-launch ordering ran out (the host-mapped
-// word is set): that launch may have left order entries or class totals
-// set, so clear them, and report the earlier solve's results as invalid.
-bool ordering_timed_out(camp_solver_t h) {
-  if (!h->h_ord_err || !*(volatile int *)h->h_ord_err) return false;
-  cudaStreamSynchronize(h->stream);
-  *(volatile int *)h->h_ord_err = 0;
-  if (h->d_ord) cudaMemset(h->d_ord, 0, h->ord_cap * sizeof(int));
-  cudaMemset(h->d_queue + 2 * (1 + kHostSolveStreams), 0, kOrdWords * sizeof(int));
-  fail(CAMP_ECUDA, "a wait of an earlier ordered solve timed out: that solve's results are invalid");
-  return true;
+// The cooperative launch of an ordered solve (or its refusal, which a test
+// can force so that the fallback below runs on any GPU).
+template <class Launch>
+cudaError_t launch_cooperative(camp_solver_t h, bool cooperative, Launch launch) {
+  if (cooperative && h->refuse_cooperative) return cudaErrorCooperativeLaunchTooLarge;
+  return launch();
 }
 
 camp_status do_solve(camp_solver_t h, int cells, const double *A_vals,
@@ -649,7 +650,6 @@ camp_status do_solve(camp_solver_t h, int cells, const double *A_vals,
     return fail(CAMP_EINVAL, "null array pointer");
   cudaError_t e = cudaSetDevice(h->device);
   if (e != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
-  if (ordering_timed_out(h)) return CAMP_ECUDA;
   View &v = (flags & CAMP_TRANSPOSE) ? h->tr : h->fwd;
 
   int arr = h->arrangement;
@@ -702,7 +702,8 @@ camp_status do_solve(camp_solver_t h, int cells, const double *A_vals,
     const int need = (a.ngroups + wpb - 1) / wpb;
     const int grid = std::max(1, std::min(need, h->sms * occ));
     set_wave(a, grid, wpb);
-    e = launch_warp(E, a, wpb, grid, smem, st);
+    e = launch_cooperative(h, a.ord_ws != nullptr,
+                           [&] { return launch_warp(E, a, wpb, grid, smem, st); });
     if (e == cudaErrorCooperativeLaunchTooLarge && a.ord_ws) {
       const camp_status rs = fall_back_to_separate_ordering(h, a, A_vals, st);
       if (rs != CAMP_OK) return rs;
@@ -751,6 +752,10 @@ camp_status camp_schedule_build(int n, int nnz, const int *row_ptr,
   if (lanes_per_cell < 1 || lanes_per_cell > 32 ||
       (lanes_per_cell & (lanes_per_cell - 1)))
     return fail(CAMP_EINVAL, "lanes_per_cell must be a power of two in [1, 32]");
+  if (row_ptr[0] != 0) return fail(CAMP_EPATTERN, "row_ptr[0] must be 0");
+  for (int i = 0; i < n; ++i)
+    if (row_ptr[i + 1] < row_ptr[i] || row_ptr[i + 1] > nnz)
+      return fail(CAMP_EPATTERN, "row_ptr not nondecreasing within [0, nnz] at row %d", i);
   std::vector<int> rp(row_ptr, row_ptr + n + 1), ci(col_idx, col_idx + nnz), diag(n, -1);
   for (int i = 0; i < n; ++i) {
     for (int k = rp[i]; k < rp[i + 1]; ++k)
@@ -783,6 +788,7 @@ camp_status camp_solver_create(camp_solver_t *out, int n, int nnz,
   std::vector<int> diag(n, -1);
   for (int i = 0; i < n; ++i) {
     if (row_ptr[i + 1] < row_ptr[i]) return fail(CAMP_EPATTERN, "row_ptr decreases at row %d", i);
+    if (row_ptr[i + 1] > nnz) return fail(CAMP_EPATTERN, "row_ptr[%d] exceeds nnz", i + 1);
     for (int k = row_ptr[i]; k < row_ptr[i + 1]; ++k) {
       const int j = col_idx[k];
       if (j < 0 || j >= n) return fail(CAMP_EPATTERN, "column %d out of range at entry %d", j, k);
@@ -919,6 +925,25 @@ camp_status camp_solver_set_ordering(camp_solver_t h, int ordering) {
   if (!h) return fail(CAMP_EINVAL, "null solver handle");
   if (ordering < 0 || ordering > 2) return fail(CAMP_EINVAL, "ordering must be 0, 1 or 2");
   h->ordering = ordering;
+  return CAMP_OK;
+}
+
+camp_status camp_solver_get_fault(camp_solver_t h, int *ordering_timed_out) {
+  if (!h || !ordering_timed_out) return fail(CAMP_EINVAL, "null argument");
+  *ordering_timed_out = 0;
+  if (h->h_ord_err && *(volatile int *)h->h_ord_err) {
+    *ordering_timed_out = 1;
+    *(volatile int *)h->h_ord_err = 0;
+  }
+  return CAMP_OK;
+}
+
+camp_status camp_solver_set_test_hooks(camp_solver_t h, long long ordering_wait_cycles,
+                                       int refuse_cooperative) {
+  if (!h) return fail(CAMP_EINVAL, "null solver handle");
+  if (ordering_wait_cycles < 0) return fail(CAMP_EINVAL, "ordering_wait_cycles < 0");
+  h->ord_wait = ordering_wait_cycles ? ordering_wait_cycles : kOrdWaitCycles;
+  h->refuse_cooperative = refuse_cooperative ? 1 : 0;
   return CAMP_OK;
 }
 
@@ -1328,7 +1353,6 @@ camp_status camp_solver_solve_mixed(camp_solver_t h, int cells,
     return fail(CAMP_EINVAL, "null array pointer");
   cudaError_t e = cudaSetDevice(h->device);
   if (e != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
-  if (ordering_timed_out(h)) return CAMP_ECUDA;
   View &v = h->fwd;
   int Lc = (h->arrangement == CAMP_ARR_WARP) ? h->lanes : auto_lanes(v.n, kAutoRowsPerLaneMixed);
   if (Lc == 0) return fail(CAMP_EUNSUPPORTED, "no warp arrangement fits n=%d", v.n);
@@ -1366,7 +1390,8 @@ camp_status camp_solver_solve_mixed(camp_solver_t h, int cells,
   const int need = (a.ngroups + wpb - 1) / wpb;
   const int grid = std::max(1, std::min(need, h->sms * occ));
   set_wave(a, grid, wpb);
-  e = launch_mixed(E, a, wpb, grid, smem, h->stream);
+  e = launch_cooperative(h, a.ord_ws != nullptr,
+                         [&] { return launch_mixed(E, a, wpb, grid, smem, h->stream); });
   if (e == cudaErrorCooperativeLaunchTooLarge && a.ord_ws) {
     const camp_status rs = fall_back_to_separate_ordering(h, a, A_vals, h->stream);
     if (rs != CAMP_OK) return rs;
@@ -1705,6 +1730,7 @@ camp_status camp_solve_noalloc(int n, int nnz, const int *row_ptr,
   for (int i = 0; i < n; ++i) {
     g_noalloc_diag[i] = -1;
     if (row_ptr[i + 1] < row_ptr[i]) return fail(CAMP_EPATTERN, "row_ptr decreases at row %d", i);
+    if (row_ptr[i + 1] > nnz) return fail(CAMP_EPATTERN, "row_ptr[%d] exceeds nnz", i + 1);
     for (int k = row_ptr[i]; k < row_ptr[i + 1]; ++k) {
       const int j = col_idx[k];
       if (j < 0 || j >= n) return fail(CAMP_EPATTERN, "column %d out of range at entry %d", j, k);
@@ -1732,8 +1758,16 @@ camp_status camp_solve_noalloc(int n, int nnz, const int *row_ptr,
                 kNoAllocScratchBytes, Lc, n);
   if (cells == 0) return CAMP_OK;
 
+  cudaStream_t st = (cudaStream_t)stream;
+  // a captured copy would read the host buffers above at replay time, after
+  // later calls may have overwritten them
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  cudaError_t e = cudaStreamIsCapturing(st, &cap);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaStreamIsCapturing");
+  if (cap != cudaStreamCaptureStatusNone)
+    return fail(CAMP_EUNSUPPORTED, "camp_solve_noalloc does not run while its stream is capturing");
   int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
+  e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
   if (dev < 0 || dev >= kNoAllocMaxDevices) return fail(CAMP_EUNSUPPORTED, "device ordinal %d", dev);
   if (!g_noalloc_dev[dev]) {  // set-up, once per device, with that device current
@@ -1771,7 +1805,6 @@ camp_status camp_solve_noalloc(int n, int nnz, const int *row_ptr,
   if ((e = warp_occupancy(E, wpb, smem, &occ)) != cudaSuccess) return cuda_fail(e, "occupancy");
   if (occ < 1) occ = 1;
   const int grid = std::max(1, std::min((a.ngroups + wpb - 1) / wpb, sms * occ));
-  cudaStream_t st = (cudaStream_t)stream;
   // stage the schedule pieces (pageable source: each call returns once its
   // host buffer has been consumed)
   if ((e = cudaMemcpyAsync(scratch, g_noalloc_dslot, (size_t)n * sizeof(int),

@@ -415,13 +415,23 @@ __device__ __forceinline__ double seg_sum_x(double v, int Lc) {
   else return seg_sum_exact(v, Lc);
 }
 
+// A bounded wait ran out: raise the launch's time-out flag (device memory,
+// read by the launch's last warp) and the host-mapped error word.
+__device__ __forceinline__ void wait_timed_out(int *flag, int *err) {
+  atomicExch(flag, 1);
+  if (err) {
+    *(volatile int *)err = 1;
+    __threadfence_system();
+  }
+}
+
 // Grid barrier of a cooperative launch, bounded in time: the CTA's threads
 // meet, thread 0 publishes the CTA's writes and counts it in, then waits
-// until the counter reaches target.  A wait longer than ~2^31 clocks (about a
-// second; the CTAs of a cooperative launch are all resident, so a legitimate
-// wait is microseconds) sets the host-mapped error word and goes on.
+// until the counter reaches target.  A wait longer than `limit` clocks (by
+// default about a second; the CTAs of a cooperative launch are all resident,
+// so a legitimate wait is microseconds) raises the time-out flags and goes on.
 __device__ __forceinline__ void grid_barrier_bounded(unsigned *ctr, unsigned target,
-                                                            int *err) {
+                                                     int *flag, int *err, long long limit) {
   __syncthreads();
   if (threadIdx.x == 0) {
     __threadfence();
@@ -431,11 +441,8 @@ __device__ __forceinline__ void grid_barrier_bounded(unsigned *ctr, unsigned tar
       unsigned v;
       asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(ctr) : "memory");
       if (v >= target) break;
-      if (clock64() - t0 > (1ll << 31)) {
-        if (err) {
-          *(volatile int *)err = 1;
-          __threadfence_system();
-        }
+      if (clock64() - t0 > limit) {
+        wait_timed_out(flag, err);
         break;
       }
       __nanosleep(64);
@@ -511,7 +518,7 @@ __device__ __forceinline__ void order_prologue(const Args &a, int *sm) {
   if (a.ord_hits && threadIdx.x == 0 && c1 > c0) atomicAdd(a.ord_hits + (unsigned)*bkey, 1u);
   for (int k = threadIdx.x; k < kOrdClasses; k += blockDim.x)
     base[k] = hist[k] ? atomicAdd(a.ord_ws + k, hist[k]) : 0;
-  grid_barrier_bounded(ctr, gridDim.x, a.ord_err);
+  grid_barrier_bounded(ctr, gridDim.x, a.ord_ws + kOrdFlag, a.ord_err, a.ord_wait);
   if (threadIdx.x < 32) {
     // exclusive prefix of the class totals, two classes per lane
     const int l = threadIdx.x;
@@ -538,17 +545,15 @@ __device__ __forceinline__ void order_prologue(const Args &a, int *sm) {
 // Wait, bounded in time as the barrier, until the in-launch ordering has
 // written order entry *p.  The entry is the only datum passed, so a relaxed
 // load suffices (an acquire would also invalidate the SM's L1 each time).
-__device__ __forceinline__ void wait_order_entry(const int *p, int *err) {
+__device__ __forceinline__ void wait_order_entry(const int *p, int *flag, int *err,
+                                                 long long limit) {
   const long long t0 = clock64();
   for (;;) {
     int v;
     asm volatile("ld.relaxed.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
     if (v != 0) return;
-    if (clock64() - t0 > (1ll << 31)) {
-      if (err) {
-        *(volatile int *)err = 1;
-        __threadfence_system();
-      }
+    if (clock64() - t0 > limit) {
+      wait_timed_out(flag, err);
       return;
     }
     __nanosleep(32);
@@ -589,22 +594,40 @@ __device__ __forceinline__ bool await_order_entries(const Args &a, unsigned g, i
   if (!a.ord_ws) return false;
   const int p = (int)g * k + lane;
   const bool mine = lane < k && p < a.cells;
-  if (mine) wait_order_entry(a.order + p, a.ord_err);
+  if (mine) wait_order_entry(a.order + p, a.ord_ws + kOrdFlag, a.ord_err, a.ord_wait);
   __syncwarp();
   return mine;
 }
 
-// End of a launch with the dynamic queue: the last warp to finish (every
-// other warp has taken its last group before counting itself done) resets
-// the queue pair and, after an in-launch ordering (every CTA is past its
-// barrier), the ordering's class totals and barrier counter, so both are
-// ready for the next launch in stream order.
+// End of a launch with the dynamic queue, called by every lane of every
+// warp once it has no group left: the last warp to finish (every other warp
+// has taken its last group before counting itself done, so every CTA is past
+// its ordering prologue) resets the queue pair and, after an in-launch
+// ordering, the ordering's workspace, so both are ready for the next launch
+// in stream order.  If a wait of the ordering ran out, the order may have
+// sent some cells to no warp and others to two: that warp then marks every
+// cell of the launch CAMP_CELL_INVALID (status, when given) with a NaN
+// residual and clears the order entries the launch left set.
 template <class Args>
 __device__ __forceinline__ void finish_queue(const Args &a, bool ordered, int warps_total,
                                              int lane) {
-  if (lane != 0) return;
+  unsigned last = 0;
+  if (lane == 0) {
+    __threadfence();
+    last = atomicAdd(a.queue + 1, 1u) == (unsigned)warps_total - 1u ? 1u : 0u;
+  }
+  last = __shfl_sync(kFull, last, 0);
+  if (!last) return;
   __threadfence();
-  if (atomicAdd(a.queue + 1, 1u) == (unsigned)warps_total - 1u) {
+  if (ordered && a.ord_ws && __ldcg(a.ord_ws + kOrdFlag) != 0) {
+    const double nan = __longlong_as_double(0x7ff8000000000000ll);
+    for (int c = lane; c < a.cells; c += 32) {
+      a.ord_out[c] = 0;
+      a.resid[c] = nan;
+      if (a.status) a.status[c] = CAMP_CELL_INVALID;
+    }
+  }
+  if (lane == 0) {
     atomicExch(a.queue, 0u);
     atomicExch(a.queue + 1, 0u);
     if (ordered && a.ord_ws)

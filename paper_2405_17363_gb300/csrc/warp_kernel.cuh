@@ -569,7 +569,7 @@ __device__ __forceinline__ void plain_launch_body(const WarpArgs &a) {
       const int p = (int)g * (LC ? 32 / LC : a.k) + lane;
       const bool mine =
           SRC == kSrcStaged && a.ord_ws && lane < (LC ? 32 / LC : a.k) && p < a.cells;
-      if (mine) wait_order_entry(a.order + p, a.ord_err);
+      if (mine) wait_order_entry(a.order + p, a.ord_ws + kOrdFlag, a.ord_err, a.ord_wait);
       __syncwarp();
       solve_group<E, SRC, LC>(a, (int)g, wbase, sch);
       if (mine) a.ord_out[p] = 0;
@@ -587,18 +587,9 @@ __device__ __forceinline__ void plain_launch_body(const WarpArgs &a) {
     run(std::integral_constant<int, 0>());
   }
   if (!a.queue) return;
-  if (lane == 0) {
-    // every other warp has taken its last group before counting itself done,
-    // so the last one may reset the queue for the next launch
-    __threadfence();
-    if (atomicAdd(a.queue + 1, 1u) == (unsigned)warps_total - 1u) {
-      atomicExch(a.queue, 0u);
-      atomicExch(a.queue + 1, 0u);
-      // every CTA is past the ordering barrier: clear the workspace
-      if (SRC == kSrcStaged && a.ord_ws)
-        for (int i = 0; i < kOrdWords; ++i) atomicExch(a.ord_ws + i, 0);
-    }
-  }
+  // the last warp resets the queue and the ordering workspace (and, after a
+  // time-out of the ordering, marks the launch's cells invalid)
+  finish_queue(a, SRC == kSrcStaged, warps_total, lane);
 }
 
 template <int E>

@@ -145,3 +145,53 @@ def test_spmv_schedule_replays_the_product(lib, wid):
         # balance: no lane exceeds the mean by more than the longest row
         lens = np.diff(m.row_ptr)
         assert L.value <= int(np.ceil(m.nnz / lc)) + lens.max()
+
+
+def test_row_ptr_rising_past_nnz_is_rejected_before_reading_columns(lib):
+    """A row_ptr that rises above nnz in the middle and comes back to nnz at
+    the end is rejected on that row, before any column index beyond nnz is
+    read: by camp_solver_create, camp_schedule_build and camp_solve_noalloc
+    (with zero cells its checks run without a GPU)."""
+    EPATTERN = -4
+    n, nnz = 3, 3
+    rp = np.array([0, 3, 3, 3], np.int32)
+    rp_bad = np.array([0, 1, 60, 3], np.int32)   # rises to 60 > nnz, not monotone
+    rp_bad2 = np.array([0, 2, 50, 50], np.int32)  # monotone, past nnz, ends != nnz
+    ci = np.array([0, 1, 2], np.int32)
+    for r in (rp_bad, rp_bad2):
+        code, h = _create(lib, n, r, ci)
+        assert code == EPATTERN and not h.value
+    # rows past nnz in the middle, back to nnz at the end
+    rp_mid = np.array([0, 1, 2, 3], np.int32)
+    rp_mid_bad = np.array([0, 40, 40, 3], np.int32)
+    code, _ = _create(lib, n, rp_mid_bad, ci)
+    assert code == EPATTERN and ("exceeds" in _msg(lib) or "decreases" in _msg(lib))
+    f = lib.camp_schedule_build
+    f.restype = ctypes.c_int
+    f.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
+                  ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]
+    L = ctypes.c_int()
+    assert f(n, nnz, rp_mid_bad.ctypes.data, ci.ctypes.data, 1, None, 0, ctypes.byref(L)) == EPATTERN
+    g = lib.camp_solve_noalloc
+    g.restype = ctypes.c_int
+    P, I, D = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+    g.argtypes = [I, I, P, P, I, P, P, P, D, I, P, P, P, P]
+    assert g(n, nnz, rp_mid_bad.ctypes.data, ci.ctypes.data, 0, None, None, None, 1e-10, 10,
+             None, None, None, None) == EPATTERN
+    assert "exceeds" in _msg(lib)
+    # the valid diagonal pattern passes every check (no cells: no GPU work)
+    assert g(n, nnz, rp_mid.ctypes.data, ci.ctypes.data, 0, None, None, None, 1e-10, 10,
+             None, None, None, None) == 0
+    del rp
+
+
+def test_testing_hooks_validate_without_gpu(lib):
+    EINVAL = -1
+    f = lib.camp_solver_set_test_hooks
+    f.restype = ctypes.c_int
+    f.argtypes = [ctypes.c_void_p, ctypes.c_longlong, ctypes.c_int]
+    assert f(None, 0, 0) == EINVAL
+    q = lib.camp_solver_get_fault
+    q.restype = ctypes.c_int
+    q.argtypes = [ctypes.c_void_p, ctypes.c_void_p]
+    assert q(None, None) == EINVAL
