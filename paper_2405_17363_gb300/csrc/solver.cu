@@ -13,6 +13,7 @@
 
 #include "camp_internal.h"
 #include "camp_testing.h"
+#include "schedule.h"
 
 namespace camp {
 cudaError_t launch_warp_1(const WarpArgs &, int, int, size_t, cudaStream_t);
@@ -188,12 +189,12 @@ camp_status cuda_fail(cudaError_t e, const char *where) {
   return fail(CAMP_ECUDA, "%s: %s", where, cudaGetErrorString(e));
 }
 
-// Balanced static SpMV schedule for lanes_per_cell lanes: whole rows are
-// assigned to lanes by longest-processing-time-first bin packing, then each
-// lane's rows are listed entry by entry and padded to the longest lane.  For
-// every slot: the packed word (column, row, end of row), the entry of the
-// cell's A row it multiplies (src; the transposed view maps through its
-// permutation), and for every row the slot of its diagonal entry.
+// Balanced static SpMV schedule for lanes_per_cell lanes (sched::build in
+// schedule.h: whole rows bin-packed onto lanes, the entries of a row ordered
+// so that a slot's gathers fall on distinct shared-memory banks).  For every
+// slot: the packed word (column, row, end of row), the entry of the cell's A
+// row it multiplies (src; the transposed view maps through its permutation),
+// and for every row the slot of its diagonal entry.
 struct Schedule {
   int Lc = 0, L = 0;
   std::vector<SchedWord> words;  // [L][Lc]
@@ -208,42 +209,29 @@ struct Schedule {
 Schedule build_schedule(int n, const std::vector<int> &rp,
                         const std::vector<int> &ci, const std::vector<int> &perm,
                         const std::vector<int> &diag, int Lc) {
-  // longest rows first onto the least-loaded lane
-  std::vector<int> order(n);
-  std::iota(order.begin(), order.end(), 0);
-  std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
-    return (rp[a + 1] - rp[a]) > (rp[b + 1] - rp[b]);
-  });
-  std::vector<long> load(Lc, 0);
-  std::vector<std::vector<int>> rows(Lc);
-  for (int r : order) {
-    int best = 0;
-    for (int q = 1; q < Lc; ++q)
-      if (load[q] < load[best]) best = q;
-    load[best] += rp[r + 1] - rp[r];
-    rows[best].push_back(r);
-  }
+  std::vector<int> order(n), bin_rows((size_t)Lc * n), bin_count(Lc), cursor(Lc), cur_row(Lc),
+      rem((size_t)Lc * n), rem_count(Lc);
+  std::vector<long> load(Lc);
+  const sched::Work w = {order.data(), load.data(), bin_rows.data(), bin_count.data(),
+                         cursor.data(), cur_row.data(), rem.data(), rem_count.data()};
+  long total = 0;  // an upper bound of L * Lc: every row on one lane
+  for (int r = 0; r < n; ++r) total += rp[r + 1] - rp[r];
+  std::vector<SchedWord> words((size_t)total * Lc);
+  std::vector<int> entry((size_t)total * Lc);
   Schedule S;
   S.Lc = Lc;
-  S.L = (int)*std::max_element(load.begin(), load.end());
-  S.words.assign((size_t)S.L * Lc, 0u);
-  S.src.assign((size_t)S.L * Lc, -1);
   S.dslot.assign(n, -1);
-  S.dst.assign(rp[n], -1);
   S.padfrom.assign(Lc, 0);
-  for (int q = 0; q < Lc; ++q) {
-    S.padfrom[q] = (int)load[q];
-    std::sort(rows[q].begin(), rows[q].end());
-    int j = 0;
-    for (int r : rows[q])
-      for (int k = rp[r]; k < rp[r + 1]; ++k, ++j) {
-        const size_t t = (size_t)j * Lc + q;
-        S.words[t] = (unsigned)ci[k] | ((unsigned)r << 11) |
-                     (k == rp[r + 1] - 1 ? kSlotEnd : 0u);
-        S.src[t] = perm.empty() ? k : perm[k];
-        S.dst[S.src[t]] = (int)t;
-        if (k == diag[r]) S.dslot[r] = (int)t;
-      }
+  S.L = sched::build(n, rp.data(), ci.data(), diag.data(), Lc, words.size(), w, words.data(),
+                     entry.data(), S.dslot.data(), S.padfrom.data());
+  const size_t slots = (size_t)S.L * Lc;
+  S.words.assign(words.begin(), words.begin() + slots);
+  S.src.assign(slots, -1);
+  S.dst.assign(rp[n], -1);
+  for (size_t t = 0; t < slots; ++t) {
+    if (entry[t] < 0) continue;
+    S.src[t] = perm.empty() ? entry[t] : perm[entry[t]];
+    S.dst[S.src[t]] = (int)t;
   }
   return S;
 }
@@ -393,13 +381,16 @@ int ilog2(int v) {
 }
 
 // Doubles from one cell's shared-memory block to the next: at least `need`,
-// and offset modulo 16 doubles (one pass over the 32 four-byte banks) so that
-// the k cells of a warp, which read the same relative addresses in the same
-// instruction, start on different banks.
+// and Lc = 32/k doubles modulo 16 (one pass over the 32 four-byte banks), so
+// that the 16/Lc cells that share a half-warp, which read the same relative
+// addresses in the same instruction, sit Lc bank pairs apart: their
+// consecutive accesses (Lc doubles per cell) tile the 16 bank pairs, and the
+// schedule's gathers (columns of distinct residues modulo Lc, schedule.h)
+// stay conflict-free.
 int bank_spread_stride(int need, int k) {
-  const int want = k >= 16 ? 1 : 16 / k;
+  const int want = (32 / k) % 16;
   int s = need;
-  while (s % 16 != want % 16) ++s;
+  while (s % 16 != want) ++s;
   return s;
 }
 
@@ -1635,69 +1626,28 @@ void *g_noalloc_dev[kNoAllocMaxDevices];              // device address of the s
 SchedWord g_noalloc_words[kNoAllocScratchBytes / sizeof(SchedWord)];
 int g_noalloc_dst[kNoAllocScratchBytes / sizeof(int)];
 int g_noalloc_padfrom[32];
+int g_noalloc_entry[kNoAllocScratchBytes / sizeof(SchedWord)];
 int g_noalloc_order[1024], g_noalloc_diag[1024], g_noalloc_dslot[1024];
 int g_noalloc_bin_rows[32][1024], g_noalloc_bin_count[32];
+int g_noalloc_rem[32][1024], g_noalloc_rem_count[32], g_noalloc_cursor[32], g_noalloc_cur_row[32];
 long g_noalloc_load[32];
 
-// Same schedule as build_schedule (longest-first bin packing of whole rows,
-// ties to the lower lane, rows ascending within a lane), written into the
-// static host buffers (slot words, slot of every entry, first padding slot of
-// every lane, slot of every diagonal); returns slots per lane or -1 if it needs
-// more than cap_slots slots.
+// Same schedule as build_schedule (sched::build, with the static host
+// buffers as its work space), written into the static host buffers (slot
+// words, slot of every entry, first padding slot of every lane, slot of
+// every diagonal); returns slots per lane or -1 if it needs more than
+// cap_slots slots.
 int noalloc_schedule(int n, const int *rp, const int *ci, int Lc, size_t cap_slots) {
-  for (int i = 0; i < n; ++i) g_noalloc_order[i] = i;
-  for (int i = 1; i < n; ++i) {  // stable insertion sort, longer rows first
-    const int r = g_noalloc_order[i];
-    const int len = rp[r + 1] - rp[r];
-    int j = i - 1;
-    while (j >= 0 && rp[g_noalloc_order[j] + 1] - rp[g_noalloc_order[j]] < len) {
-      g_noalloc_order[j + 1] = g_noalloc_order[j];
-      --j;
-    }
-    g_noalloc_order[j + 1] = r;
-  }
-  for (int q = 0; q < Lc; ++q) {
-    g_noalloc_load[q] = 0;
-    g_noalloc_bin_count[q] = 0;
-  }
-  for (int i = 0; i < n; ++i) {
-    const int r = g_noalloc_order[i];
-    int best = 0;
-    for (int q = 1; q < Lc; ++q)
-      if (g_noalloc_load[q] < g_noalloc_load[best]) best = q;
-    g_noalloc_load[best] += rp[r + 1] - rp[r];
-    g_noalloc_bin_rows[best][g_noalloc_bin_count[best]++] = r;
-  }
-  long L = 0;
-  for (int q = 0; q < Lc; ++q) L = std::max(L, g_noalloc_load[q]);
-  if ((size_t)L * Lc > cap_slots) return -1;
-  for (long w = 0; w < L * Lc; ++w) g_noalloc_words[w] = 0u;
-  for (int q = 0; q < Lc; ++q) {
-    g_noalloc_padfrom[q] = (int)g_noalloc_load[q];
-    int *rows = g_noalloc_bin_rows[q];
-    const int cnt = g_noalloc_bin_count[q];
-    for (int i = 1; i < cnt; ++i) {  // ascending row order within the lane
-      const int r = rows[i];
-      int j = i - 1;
-      while (j >= 0 && rows[j] > r) {
-        rows[j + 1] = rows[j];
-        --j;
-      }
-      rows[j + 1] = r;
-    }
-    long j = 0;
-    for (int t = 0; t < cnt; ++t) {
-      const int r = rows[t];
-      for (int k = rp[r]; k < rp[r + 1]; ++k, ++j) {
-        const long slot = j * Lc + q;
-        g_noalloc_words[slot] = (unsigned)ci[k] | ((unsigned)r << 11) |
-                                (k == rp[r + 1] - 1 ? kSlotEnd : 0u);
-        g_noalloc_dst[k] = (int)slot;
-        if (k == g_noalloc_diag[r]) g_noalloc_dslot[r] = (int)slot;
-      }
-    }
-  }
-  return (int)L;
+  const sched::Work w = {g_noalloc_order, g_noalloc_load, &g_noalloc_bin_rows[0][0],
+                         g_noalloc_bin_count, g_noalloc_cursor, g_noalloc_cur_row,
+                         &g_noalloc_rem[0][0], g_noalloc_rem_count};
+  const size_t cap = std::min(cap_slots, sizeof(g_noalloc_words) / sizeof(g_noalloc_words[0]));
+  const int L = sched::build(n, rp, ci, g_noalloc_diag, Lc, cap, w, g_noalloc_words,
+                             g_noalloc_entry, g_noalloc_dslot, g_noalloc_padfrom);
+  if (L < 0) return -1;
+  for (long t = 0; t < (long)L * Lc; ++t)
+    if (g_noalloc_entry[t] >= 0) g_noalloc_dst[g_noalloc_entry[t]] = (int)t;
+  return L;
 }
 
 }  // namespace
