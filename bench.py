@@ -253,18 +253,40 @@ def time_e2e(camp, solver, cb, C, tol, maxit, steps, world, dev):
             "d2h_bytes_per_step": C * (m.n * 8 + 4 + 8 + 4)}
 
 
-def time_uneven(camp, dev, flush, stream, steps=50):
+def difficulty_order(mech, A):
+    """Host model of the library's cell ordering: the difficulty class of a
+    cell (half octaves of max_i |A_ii - 1|, from the high word of its bit
+    pattern; class 0 hardest) and the cells sorted hardest class first (index
+    order inside a class; the kernels' order inside a class is arbitrary)."""
+    d = np.abs(A[:, mech.diag_pos()] - 1.0).max(axis=1)
+    hi = (np.ascontiguousarray(d).view(np.uint64) >> np.uint64(32)).astype(np.int64)
+    top = ((1023 + 3) << 1) | 1
+    cls = np.clip(top - (hi >> 19), 0, 63)
+    return np.argsort(cls, kind="stable")
+
+
+def time_uneven(camp, dev, flush, stream, steps=50, tune=True):
     """The uneven-batching workload (40/90 x 20000 + 80/200 x 5000 + 150/400 x
-    500 cells, gamma up to 1): one persistent launch under a CUDA graph against
-    three plain FP64 launches back to back, both to the 1e-10 true residual."""
+    500 cells, gamma up to 1): the persistent launch under a CUDA graph with
+    the launch configuration picked by the autotuner (tune.tune_batch, timed
+    here with each mechanism's cells ordered hardest first), the same in index
+    order, and three plain FP64 launches back to back, all to the 1e-10 true
+    residual.  Lockstep waste per mechanism (lane-iterations spent waiting for
+    the slowest cell of a warp, over useful ones) for index order and for the
+    host model of the hardest-first order."""
     import torch
+    from paper_2405_17363_gb300 import tune as tuner
     cbs, tol, maxit = synth.workload(2)
     solvers = [camp.Solver(cb.mech.row_ptr, cb.mech.col_idx) for cb in cbs]
     A = [torch.as_tensor(cb.A_vals, device=dev) for cb in cbs]
     b = [torch.as_tensor(cb.b, device=dev) for cb in cbs]
     batch = camp.Batch(solvers)
+    tuned = tuner.tune_batch(batch, A, b, tol, maxit, reps=3) if tune else None
     out = batch.solve(A, b, tol, maxit)
     t_batch = time_steps(lambda: batch.solve(A, b, tol, maxit, out=out), flush, stream, steps, 3)
+    batch.set_ordering(0)
+    t_index = time_steps(lambda: batch.solve(A, b, tol, maxit, out=out), flush, stream, steps, 3)
+    batch.set_ordering(1)
     outs = [sv.solve(a, v, tol, maxit) for sv, a, v in zip(solvers, A, b)]
 
     def plain():
@@ -272,16 +294,178 @@ def time_uneven(camp, dev, flush, stream, steps=50):
             sv.solve(a, v, tol, maxit, out=o)
     t_plain = time_steps(plain, flush, stream, steps, 3)
     cells = sum(cb.cells for cb in cbs)
-    mb, mp = sum(t_batch) / steps, sum(t_plain) / steps
+    mb, mi, mp = (sum(t) / steps for t in (t_batch, t_index, t_plain))
     conv = sum(int((o[3] == 0).sum().item()) for o in out)
-    iters = np.concatenate([o[1].cpu().numpy() for o in out])
+    its = [o[1].cpu().numpy() for o in out]
+    iters = np.concatenate(its)
+    waste = {"index": [], "hardest_first": []}
+    for cb, it in zip(cbs, its):
+        k = 32 // sv_lanes(cb.mech.n)
+        waste["index"].append(lockstep_waste(it, k))
+        waste["hardest_first"].append(lockstep_waste(it[difficulty_order(cb.mech, cb.A_vals)], k))
     batch.close()
     for sv in solvers:
         sv.close()
-    return {"workload": synth.WORKLOADS[2][0], "cells": cells,
-            "persistent_graph": {"ms_per_step": mb, "value": cells / (mb * 1e-3), "unit": UNIT},
-            "three_plain_launches": {"ms_per_step": mp, "value": cells / (mp * 1e-3), "unit": UNIT},
-            "converged": conv, "iters_mean": float(iters.mean()), "iters_max": int(iters.max())}
+    res = {"workload": synth.WORKLOADS[2][0], "cells": cells,
+           "persistent_graph": {"ms_per_step": mb, "value": cells / (mb * 1e-3), "unit": UNIT,
+                                "ordering": "hardest first per mechanism"},
+           "persistent_graph_index_order": {"ms_per_step": mi, "value": cells / (mi * 1e-3),
+                                            "unit": UNIT},
+           "three_plain_launches": {"ms_per_step": mp, "value": cells / (mp * 1e-3), "unit": UNIT},
+           "lockstep_waste_by_mechanism": waste, "mechanisms_species": [cb.mech.n for cb in cbs],
+           "converged": conv, "iters_mean": float(iters.mean()), "iters_max": int(iters.max())}
+    if tuned is not None:
+        res["tuned_config"] = {"rows_per_lane": tuned["best"][0],
+                               "warps_per_block": tuned["best"][1],
+                               "stage_A_in_smem": tuned["best"][2],
+                               "configs_timed": len(tuned["table"])}
+    return res
+
+
+def variability(camp, dev, flush, stream, steps):
+    """'Realistic' cells (per-cell concentrations and gamma, as generated)
+    against 'ideal' cells (every cell a copy of the first one), as in the
+    paper's two initial-condition set-ups (Sec. 4.2): the spread of iteration
+    counts, the lockstep waste it causes in the warp-packed solve (index order
+    and the host model of hardest first) and the throughput of the plain
+    launches (one per mechanism, the library's default in-launch ordering) and
+    of the persistent launch (its default hardest-first ordering)."""
+    import torch
+    rows = []
+    for wid in (WORKLOAD_ID, 2):
+        cbs, tol, maxit = synth.workload(wid)
+        for setup in ("realistic", "ideal"):
+            solvers, As, bs, hostA, cells = [], [], [], [], 0
+            for cb in cbs:
+                A, b = cb.A_vals, cb.b
+                if setup == "ideal":
+                    A = np.repeat(A[:1], cb.cells, axis=0)
+                    b = np.repeat(b[:1], cb.cells, axis=0)
+                hostA.append(A)
+                solvers.append(camp.Solver(cb.mech.row_ptr, cb.mech.col_idx))
+                As.append(torch.as_tensor(np.ascontiguousarray(A), device=dev))
+                bs.append(torch.as_tensor(np.ascontiguousarray(b), device=dev))
+                cells += cb.cells
+            outs = [sv.solve(a, v, tol, maxit) for sv, a, v in zip(solvers, As, bs)]
+
+            def plain():
+                for sv, a, v, o in zip(solvers, As, bs, outs):
+                    sv.solve(a, v, tol, maxit, out=o)
+            tp = sum(time_steps(plain, flush, stream, steps, 3)) / steps
+            batch = camp.Batch(solvers)
+            bo = batch.solve(As, bs, tol, maxit)
+            tb = sum(time_steps(lambda: batch.solve(As, bs, tol, maxit, out=bo), flush, stream,
+                                steps, 3)) / steps
+            its = [o[1].cpu().numpy() for o in outs]
+            it = np.concatenate(its)
+            w_idx, w_ord = [], []
+            for cb, A, i1 in zip(cbs, hostA, its):
+                k = 32 // sv_lanes(cb.mech.n)
+                w_idx.append(lockstep_waste(i1, k))
+                w_ord.append(lockstep_waste(i1[difficulty_order(cb.mech, A)], k))
+            rows.append({"workload": synth.WORKLOADS[wid][0], "setup": setup, "cells": cells,
+                         "iters_mean": float(it.mean()), "iters_std": float(it.std()),
+                         "iters_p99": float(np.percentile(it, 99)), "iters_max": int(it.max()),
+                         "lockstep_waste_index_order": w_idx,
+                         "lockstep_waste_hardest_first": w_ord,
+                         "plain_ms": tp, "plain_value": cells / (tp * 1e-3),
+                         "persistent_ms": tb, "persistent_value": cells / (tb * 1e-3)})
+            batch.close()
+            for sv in solvers:
+                sv.close()
+    return rows
+
+
+def time_cfg4(camp, dev, flush, stream, steps=10, threads=None):
+    """The mixed-precision workload at full size (150 species / 400 reactions,
+    100,000 cells, gamma logU[1e-4,1e-1]): the FP32-inner refinement against
+    the plain FP64 solve, both to the 1e-10 true residual, in cells/s; and the
+    per-cell relative error ||x - x_oracle|| / ||x_oracle|| of both against
+    the FP64 oracle over all cells (max and p99; the oracle runs outside the
+    timed regions)."""
+    import torch
+    import oracle
+    cbs, tol, maxit = synth.workload(4)
+    cb = cbs[0]
+    m = cb.mech
+    C = cb.cells
+    s = camp.Solver(m.row_ptr, m.col_idx)
+    A = torch.as_tensor(cb.A_vals, device=dev)
+    b = torch.as_tensor(cb.b, device=dev)
+    f64 = s.solve(A, b, tol, maxit)
+    t64 = sum(time_steps(lambda: s.solve(A, b, tol, maxit, out=f64), flush, stream, steps, 3)) / steps
+    mix = s.solve_mixed(A, b, tol)
+    t32 = sum(time_steps(lambda: s.solve_mixed(A, b, tol, out=mix), flush, stream, steps, 3)) / steps
+    torch.cuda.synchronize()
+    x64 = f64[0].cpu().numpy()
+    x32 = mix[0].cpu().numpy()
+    orc = oracle.solve(m.row_ptr, m.col_idx, cb.A_vals, cb.b, tol, maxit,
+                       threads=threads or os.cpu_count() or 1)
+    nrm = np.linalg.norm(orc["x"], axis=1)
+    e32 = np.linalg.norm(x32 - orc["x"], axis=1) / nrm
+    e64 = np.linalg.norm(x64 - orc["x"], axis=1) / nrm
+    res = {"workload": synth.WORKLOADS[4][0], "cells": C, "n": m.n, "nnz": m.nnz, "tol": tol,
+           "fp32_inner": {"ms_per_step": t32, "value": C / (t32 * 1e-3), "unit": UNIT,
+                          "converged": int((mix[4] == 0).sum().item()),
+                          "sweeps_mean": float(mix[2].double().mean().item()),
+                          "inner_iters_mean": float(mix[1].double().mean().item()),
+                          "rel_err_vs_fp64_oracle_max": float(e32.max()),
+                          "rel_err_vs_fp64_oracle_p99": float(np.percentile(e32, 99))},
+           "fp64": {"ms_per_step": t64, "value": C / (t64 * 1e-3), "unit": UNIT,
+                    "converged": int((f64[3] == 0).sum().item()),
+                    "iters_mean": float(f64[1].double().mean().item()),
+                    "rel_err_vs_fp64_oracle_max": float(e64.max()),
+                    "rel_err_vs_fp64_oracle_p99": float(np.percentile(e64, 99))},
+           "speedup_fp32_inner_vs_fp64": t64 / t32,
+           "l2": "inputs (1.0 GB) larger than L2, flushed between timed steps"}
+    s.close()
+    return res
+
+
+def time_adjoint(camp, dev, flush, stream, steps=50):
+    """The adjoint workload (80 species / 200 reactions, 10,000 cells): one
+    forward solve and the backward of L = sum_c w_c . x_c as the library's
+    autograd Function runs it (the transposed solve A^T lambda = w and
+    dL/dA_vals = -lambda[row] x[col]), through the C ABI, L2 flushed before
+    each step; cells/s of forward + backward and the backward's share."""
+    import torch
+    cbs, tol, maxit = synth.workload(3)
+    cb = cbs[0]
+    m = cb.mech
+    C = cb.cells
+    s = camp.Solver(m.row_ptr, m.col_idx)
+    A = torch.as_tensor(cb.A_vals, device=dev)
+    b = torch.as_tensor(cb.b, device=dev)
+    w = torch.as_tensor(np.random.default_rng(3000).standard_normal((C, m.n)), device=dev)
+    x = torch.empty_like(b)
+    lam = torch.empty_like(b)
+    gA = torch.empty_like(A)
+    it = [torch.empty(C, dtype=torch.int32, device=dev) for _ in range(2)]
+    res = [torch.empty(C, dtype=torch.float64, device=dev) for _ in range(2)]
+    st = [torch.empty(C, dtype=torch.int32, device=dev) for _ in range(2)]
+
+    def fwd():
+        camp.camp_solver_solve_ex(s.h, C, A, b, x, tol, maxit, it[0], res[0], st[0], 0)
+
+    def bwd():
+        camp.camp_solver_solve_ex(s.h, C, A, w, lam, tol, maxit, it[1], res[1], st[1],
+                                  camp.CAMP_TRANSPOSE)
+        camp.camp_solver_grad_A(s.h, C, lam, x, gA)
+
+    def both():
+        fwd()
+        bwd()
+    tt = sum(time_steps(both, flush, stream, steps, 3)) / steps
+    tb = sum(time_steps(bwd, flush, stream, steps, 3)) / steps
+    out = {"workload": synth.WORKLOADS[3][0], "cells": C,
+           "value": C / (tt * 1e-3), "unit": "cells/s (forward + backward)", "ms_per_step": tt,
+           "backward_ms": tb, "backward_share": tb / tt,
+           "converged_forward": int((st[0] == 0).sum().item()),
+           "converged_transposed": int((st[1] == 0).sum().item()),
+           "iters_mean_forward": float(it[0].double().mean().item()),
+           "iters_mean_transposed": float(it[1].double().mean().item())}
+    s.close()
+    return out
 
 
 def fp64_rate(camp, dev):
@@ -395,7 +579,8 @@ def run_uneven_case(args):
 
 def lockstep_waste(iters, k):
     """Lane-iterations idle because the k cells sharing a warp run until the
-    slowest converges, as a fraction of the useful ones (cells in index order)."""
+    slowest converges, as a fraction of the useful ones (consecutive cells of
+    the given order share a warp)."""
     it = np.asarray(iters, dtype=np.float64)
     pad = (-len(it)) % k
     grp = np.concatenate([it, np.zeros(pad)]).reshape(-1, k)
@@ -403,52 +588,12 @@ def lockstep_waste(iters, k):
 
 
 def run_variability_case(args):
-    """--case variability: 'realistic' cells (per-cell concentrations and
-    gamma, as generated) against 'ideal' cells (every cell a copy of the first
-    one), as in the paper's two initial-condition set-ups (Sec. 4.2): the
-    spread of iteration counts, the lockstep waste it causes in the
-    warp-packed solve, and the throughput of the plain and persistent launches."""
+    """--case variability: the realistic vs ideal rows alone."""
     import torch
     from paper_2405_17363_gb300 import camp
     dev = torch.device("cuda", 0)
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
-    stream = torch.cuda.current_stream()
-    rows = []
-    for wid in (WORKLOAD_ID, 2):
-        cbs, tol, maxit = synth.workload(wid)
-        for setup in ("realistic", "ideal"):
-            solvers, As, bs, cells = [], [], [], 0
-            for cb in cbs:
-                A, b = cb.A_vals, cb.b
-                if setup == "ideal":
-                    A = np.repeat(A[:1], cb.cells, axis=0)
-                    b = np.repeat(b[:1], cb.cells, axis=0)
-                solvers.append(camp.Solver(cb.mech.row_ptr, cb.mech.col_idx))
-                As.append(torch.as_tensor(np.ascontiguousarray(A), device=dev))
-                bs.append(torch.as_tensor(np.ascontiguousarray(b), device=dev))
-                cells += cb.cells
-            outs = [sv.solve(a, v, tol, maxit) for sv, a, v in zip(solvers, As, bs)]
-
-            def plain():
-                for sv, a, v, o in zip(solvers, As, bs, outs):
-                    sv.solve(a, v, tol, maxit, out=o)
-            tp = sum(time_steps(plain, flush, stream, args.steps, 3)) / args.steps
-            batch = camp.Batch(solvers)
-            bo = batch.solve(As, bs, tol, maxit)
-            tb = sum(time_steps(lambda: batch.solve(As, bs, tol, maxit, out=bo), flush, stream,
-                                args.steps, 3)) / args.steps
-            it = np.concatenate([o[1].cpu().numpy() for o in outs])
-            waste = [lockstep_waste(o[1].cpu().numpy(), 32 // sv_lanes(sv.n))
-                     for sv, o in zip(solvers, outs)]
-            rows.append({"workload": synth.WORKLOADS[wid][0], "setup": setup, "cells": cells,
-                         "iters_mean": float(it.mean()), "iters_std": float(it.std()),
-                         "iters_p99": float(np.percentile(it, 99)), "iters_max": int(it.max()),
-                         "lockstep_waste_by_mechanism": waste,
-                         "plain_ms": tp, "plain_value": cells / (tp * 1e-3),
-                         "persistent_ms": tb, "persistent_value": cells / (tb * 1e-3)})
-            batch.close()
-            for sv in solvers:
-                sv.close()
+    rows = variability(camp, dev, flush, torch.cuda.current_stream(), args.steps)
     print(json.dumps({"case": "variability", "unit": UNIT, "rows": rows}), flush=True)
 
 
@@ -599,7 +744,7 @@ def main():
 
     mixed_side = None
     e2e = None
-    uneven = None
+    uneven = var_rows = cfg4 = adjoint = None
     fused = None
     newton = None
     fp64_measured = None
@@ -619,7 +764,11 @@ def main():
         fp64_measured = fp64_rate(camp, dev)
         fused = time_fused(camp, cb, tol, maxit, flush, stream, dev)
         newton = time_newton(camp, cb, flush, stream, dev)
-        uneven = time_uneven(camp, dev, flush, stream) if rank == 0 else None
+        if rank == 0:
+            uneven = time_uneven(camp, dev, flush, stream)
+            var_rows = variability(camp, dev, flush, stream, 20)
+            cfg4 = time_cfg4(camp, dev, flush, stream)
+            adjoint = time_adjoint(camp, dev, flush, stream)
 
     if rank == 0:
         cpu = cpu_baseline(m, cb.A_vals, cb.b, tol, maxit, args.cpu_seconds) \
@@ -663,6 +812,12 @@ def main():
             line["mixed_fp32_inner"] = mixed_side
         if uneven is not None:
             line["uneven_batch"] = uneven
+        if var_rows is not None:
+            line["variability"] = var_rows
+        if cfg4 is not None:
+            line["mixed_cfg4"] = cfg4
+        if adjoint is not None:
+            line["adjoint"] = adjoint
         if fused is not None:
             line["fused_assembly"] = fused
         if newton is not None:

@@ -269,6 +269,17 @@ camp_status camp_batch_set_config(camp_batch_t b, int rows_per_lane,
                                   int warps_per_block, int stage_A_in_smem);
 
 /*
+ * Cell ordering of the batch (the cells that share a warp run in lockstep):
+ * 1 (default) hands each mechanism's cells to warps hardest first, by the
+ * same difficulty estimate and classes as camp_solver_set_ordering (a
+ * classify and a scatter launch over all mechanisms, part of the batch's
+ * graph; device scratch of 5 bytes per cell plus 512 bytes per mechanism);
+ * 0 keeps index order.  Results are bitwise the same either way.
+ * CAMP_EINVAL for other values.
+ */
+camp_status camp_batch_set_ordering(camp_batch_t b, int ordering);
+
+/*
  * Solve cells[m] cells of every mechanism m in one launch (captured once in a
  * CUDA graph and replayed; a change of launch shape re-captures it).  The
  * arrays are HOST arrays [nmech] of DEVICE pointers with the layouts of

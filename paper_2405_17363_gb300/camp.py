@@ -63,6 +63,7 @@ _batch_create = _sig("camp_batch_create", [ctypes.POINTER(_P), _I, _P])
 _batch_destroy = _sig("camp_batch_destroy", [_P])
 _batch_set_stream = _sig("camp_batch_set_stream", [_P, _P])
 _batch_set_config = _sig("camp_batch_set_config", [_P, _I, _I, _I])
+_batch_set_ordering = _sig("camp_batch_set_ordering", [_P, _I])
 _batch_solve = _sig("camp_batch_solve", [_P, _P, _P, _P, _P, _D, _I, _P, _P, _P])
 _last_error = _sig("camp_last_error", [], ctypes.c_char_p)
 _version = _sig("camp_version", [], ctypes.c_char_p)
@@ -273,6 +274,10 @@ def camp_batch_set_config(h: int, rows_per_lane=0, warps_per_block=0, stage_A_in
            "camp_batch_set_config")
 
 
+def camp_batch_set_ordering(h: int, ordering: int):
+    _check(_batch_set_ordering(h, int(ordering)), "camp_batch_set_ordering")
+
+
 def camp_batch_solve(h, cells, A_vals, b, x, tol, maxit, iters_out, resid_out,
                      status_out=None):
     """cells: list of ints; the other arguments are lists of CUDA tensors
@@ -428,6 +433,10 @@ class Batch:
 
     def set_config(self, rows_per_lane=0, warps_per_block=0, stage_A_in_smem=1):
         camp_batch_set_config(self.h, rows_per_lane, warps_per_block, stage_A_in_smem)
+
+    def set_ordering(self, ordering: int):
+        """1 (default): each mechanism's cells hardest first; 0: index order."""
+        camp_batch_set_ordering(self.h, ordering)
 
     def solve(self, A_list, b_list, tol=1e-10, maxit=500, out=None):
         """Returns a list of (x, iters, resid, status), one per mechanism."""

@@ -179,6 +179,24 @@ cudaError_t launch_difficulty_order(const double *A, int cells, int n, int nnz,
                                     const int *diag, void *scratch, int **order,
                                     cudaStream_t st);
 
+// Difficulty ordering of a persistent multi-mechanism batch (order.cu): one
+// classify and one scatter launch over the concatenated cells of all
+// mechanisms (cell_begin: offsets, cell_begin[nmech] = total); counts holds
+// per mechanism kOrdClasses totals then kOrdClasses cursors (zero on entry);
+// order + cell_begin[m] receives mechanism m's cells, hardest class first.
+struct BatchOrderArgs {
+  int nmech;
+  const double *A[kMaxMech];
+  const int *diag[kMaxMech];
+  int n[kMaxMech], nnz[kMaxMech];
+  int cell_begin[kMaxMech + 1];
+  unsigned char *cls;
+  int *counts;
+  int *order;
+};
+const void *batch_classify_kernel_fn();  // __global__ (const BatchOrderArgs)
+const void *batch_scatter_kernel_fn();   // __global__ (const BatchOrderArgs), 1 thread per cell
+
 constexpr int kMaxE = 16;  // rows per lane supported by the warp kernel
 
 // Difficulty classes of the ordering (half octaves of max_i |A_ii - 1|) and

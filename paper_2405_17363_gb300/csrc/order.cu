@@ -62,7 +62,63 @@ __global__ void scatter_kernel(const unsigned char *__restrict__ cls, int cells,
   }
 }
 
+// The same two steps for the persistent multi-mechanism batch, all
+// mechanisms in one launch each: cell i of the concatenated cell space
+// belongs to mechanism m with cell_begin[m] <= i < cell_begin[m + 1]; every
+// mechanism has its own class totals and cursors (counts + m * 2 kClasses)
+// and its own order (order + cell_begin[m], cell indices within m).
+__global__ void batch_classify_kernel(const BatchOrderArgs a) {
+  const int lane = threadIdx.x & 31;
+  const int warps = (gridDim.x * blockDim.x) >> 5;
+  const int total = a.cell_begin[a.nmech];
+  for (int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < total; i += warps) {
+    int m = 0;
+    while (m + 1 < a.nmech && i >= a.cell_begin[m + 1]) ++m;
+    const double *Ac = a.A[m] + (size_t)(i - a.cell_begin[m]) * a.nnz[m];
+    unsigned worst = 0;
+    for (int r = lane; r < a.n[m]; r += 32) {
+      const unsigned hi = diag_departure_hi(__ldg(Ac + __ldg(a.diag[m] + r)));
+      worst = hi > worst ? hi : worst;
+    }
+    worst = __reduce_max_sync(kFull, worst);
+    if (lane == 0) {
+      const int k = difficulty_class(worst);
+      a.cls[i] = (unsigned char)k;
+      atomicAdd(a.counts + m * 2 * kClasses + k, 1);
+    }
+  }
+}
+
+__global__ void batch_scatter_kernel(const BatchOrderArgs a) {
+  __shared__ int start[kMaxMech][kClasses];
+  for (int m = threadIdx.x >> 5; m < a.nmech; m += blockDim.x >> 5) {
+    const int l = threadIdx.x & 31;
+    const int *cnt = a.counts + m * 2 * kClasses;
+    const int x = cnt[2 * l], y = cnt[2 * l + 1];
+    int s = x + y;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int t = __shfl_up_sync(kFull, s, o);
+      if (l >= o) s += t;
+    }
+    start[m][2 * l] = s - x - y;
+    start[m][2 * l + 1] = s - y;
+  }
+  __syncthreads();
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < a.cell_begin[a.nmech]) {
+    int m = 0;
+    while (m + 1 < a.nmech && i >= a.cell_begin[m + 1]) ++m;
+    const int k = a.cls[i];
+    const int pos = start[m][k] + atomicAdd(a.counts + m * 2 * kClasses + kClasses + k, 1);
+    a.order[a.cell_begin[m] + pos] = i - a.cell_begin[m];
+  }
+}
+
 }  // namespace
+
+const void *batch_classify_kernel_fn() { return (const void *)batch_classify_kernel; }
+const void *batch_scatter_kernel_fn() { return (const void *)batch_scatter_kernel; }
 
 size_t difficulty_scratch_bytes(int cells) {
   // class bytes (rounded to 16), the order, the class totals and cursors

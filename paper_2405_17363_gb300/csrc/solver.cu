@@ -730,7 +730,7 @@ camp_status do_solve(camp_solver_t h, int cells, const double *A_vals,
 extern "C" {
 
 const char *camp_last_error(void) { return g_err.c_str(); }
-const char *camp_version(void) { return "campsolve 0.11 (sm_103a)"; }
+const char *camp_version(void) { return "campsolve 0.12 (sm_103a)"; }
 
 camp_status camp_schedule_build(int n, int nnz, const int *row_ptr,
                                 const int *col_idx, int lanes_per_cell,
@@ -1409,6 +1409,15 @@ struct camp_batch {
   cudaGraphNode_t knode = nullptr;
   int g_E = 0, g_wpb = 0, g_asmem = -1, g_grid = 0;
   size_t g_smem = 0;
+  // difficulty ordering (camp_batch_set_ordering, default on): per-cell
+  // classes, the order and per-mechanism class counters, grown on demand;
+  // the graph then starts with a memset, a classify and a scatter node
+  int ordering = 1;
+  unsigned char *d_ord = nullptr;
+  size_t ord_cap = 0;  // cells
+  cudaGraphNode_t cnode = nullptr, snode = nullptr;
+  int g_ordered = -1, g_ogrid = 0, g_sgrid = 0;
+  void *g_ordbuf = nullptr;
 };
 
 static void batch_drop_graph(camp_batch *b) {
@@ -1417,7 +1426,10 @@ static void batch_drop_graph(camp_batch *b) {
   b->exec = nullptr;
   b->graph = nullptr;
   b->knode = nullptr;
+  b->cnode = nullptr;
+  b->snode = nullptr;
   b->g_asmem = -1;
+  b->g_ordered = -1;
 }
 
 camp_status camp_batch_create(camp_batch_t *out, int nmech,
@@ -1452,6 +1464,7 @@ camp_status camp_batch_destroy(camp_batch_t b) {
   cudaStreamSynchronize(b->stream);
   batch_drop_graph(b);
   cudaFree(b->d_counter);
+  cudaFree(b->d_ord);
   delete b;
   return CAMP_OK;
 }
@@ -1473,6 +1486,13 @@ camp_status camp_batch_set_config(camp_batch_t b, int rows_per_lane,
   b->E = rows_per_lane;
   b->wpb = warps_per_block;
   b->a_smem = stage_A_in_smem ? 1 : 0;
+  return CAMP_OK;
+}
+
+camp_status camp_batch_set_ordering(camp_batch_t b, int ordering) {
+  if (!b) return fail(CAMP_EINVAL, "null batch handle");
+  if (ordering < 0 || ordering > 1) return fail(CAMP_EINVAL, "ordering must be 0 or 1");
+  b->ordering = ordering;
   return CAMP_OK;
 }
 
@@ -1544,6 +1564,40 @@ camp_status camp_batch_solve(camp_batch_t b, const int *cells,
   args.total_items = items;
   args.warp_doubles = warp_doubles;
   if (items == 0) return CAMP_OK;
+  // hardest first within each mechanism (mechanisms stay largest first)
+  BatchOrderArgs oa;
+  memset(&oa, 0, sizeof oa);
+  oa.nmech = b->nmech;
+  for (int q = 0; q < b->nmech; ++q) {
+    const int m = order[q];
+    oa.A[q] = A_vals[m];
+    oa.diag[q] = b->mech[m]->fwd.d_diag;
+    oa.n[q] = b->mech[m]->n;
+    oa.nnz[q] = b->mech[m]->nnz;
+    oa.cell_begin[q + 1] = oa.cell_begin[q] + cells[m];
+  }
+  const int total_cells = oa.cell_begin[b->nmech];
+  const bool ordered = b->ordering && total_cells > 1;
+  const size_t cnt_bytes = (size_t)b->nmech * 2 * kOrdClasses * sizeof(int);
+  if (ordered) {
+    if ((size_t)total_cells > b->ord_cap) {
+      cudaFree(b->d_ord);
+      b->d_ord = nullptr;
+      b->ord_cap = 0;
+      // counters, the order (4 bytes per cell), then the classes (1 byte per cell)
+      if ((e = cudaMalloc(&b->d_ord, cnt_bytes + (size_t)total_cells * 5)) != cudaSuccess)
+        return fail(CAMP_ENOMEM, "batch ordering scratch: %s", cudaGetErrorString(e));
+      b->ord_cap = (size_t)total_cells;
+    }
+    oa.counts = (int *)b->d_ord;
+    oa.order = (int *)(b->d_ord + cnt_bytes);
+    oa.cls = b->d_ord + cnt_bytes + b->ord_cap * 4;
+    for (int q = 0; q < b->nmech; ++q) args.m[q].order = oa.order + oa.cell_begin[q];
+  }
+  const int ogrid = (int)std::max(1L, std::min(((long)total_cells * 32 + 255) / 256,
+                                                (long)b->sms * 8));
+  const int sgrid = (total_cells + 255) / 256;
+  void *oparams[] = {&oa};
   int wpb = b->wpb > 0 ? b->wpb : 4;
   size_t smem = (size_t)wpb * warp_doubles * 8;
   while (smem > b->smem_optin && wpb > 1) smem = (size_t)(--wpb) * warp_doubles * 8;
@@ -1553,10 +1607,28 @@ camp_status camp_batch_solve(camp_batch_t b, const int *cells,
   if (occ < 1) occ = 1;
   const int grid = std::max(1, std::min(b->sms * occ, (items + wpb - 1) / wpb));
   void *kparams[] = {&args};
+  cudaKernelNodeParams kp;
+  memset(&kp, 0, sizeof kp);
+  kp.func = const_cast<void *>(batch_kernel(E, asmem));
+  kp.gridDim = dim3(grid);
+  kp.blockDim = dim3(wpb * 32);
+  kp.sharedMemBytes = (unsigned)smem;
+  kp.kernelParams = kparams;
+  cudaKernelNodeParams cp, sp;
+  memset(&cp, 0, sizeof cp);
+  cp.func = const_cast<void *>(batch_classify_kernel_fn());
+  cp.gridDim = dim3(ogrid);
+  cp.blockDim = dim3(256);
+  cp.kernelParams = oparams;
+  sp = cp;
+  sp.func = const_cast<void *>(batch_scatter_kernel_fn());
+  sp.gridDim = dim3(sgrid);
   if (!b->exec || b->g_E != E || b->g_wpb != wpb || b->g_asmem != (int)asmem ||
-      b->g_grid != grid || b->g_smem != smem) {
+      b->g_grid != grid || b->g_smem != smem || b->g_ordered != (int)ordered ||
+      (ordered && (b->g_ordbuf != (void *)b->d_ord || b->g_ogrid != ogrid ||
+                   b->g_sgrid != sgrid))) {
     batch_drop_graph(b);
-    cudaGraphNode_t mnode;
+    cudaGraphNode_t mnode, onode;
     cudaMemsetParams mp;
     memset(&mp, 0, sizeof mp);
     mp.dst = b->d_counter;
@@ -1565,30 +1637,40 @@ camp_status camp_batch_solve(camp_batch_t b, const int *cells,
     mp.width = 1;
     mp.height = 1;
     mp.pitch = sizeof(unsigned int);
-    cudaKernelNodeParams kp;
-    memset(&kp, 0, sizeof kp);
-    kp.func = const_cast<void *>(batch_kernel(E, asmem));
-    kp.gridDim = dim3(grid);
-    kp.blockDim = dim3(wpb * 32);
-    kp.sharedMemBytes = (unsigned)smem;
-    kp.kernelParams = kparams;
+    cudaMemsetParams op = mp;  // the ordering's class counters
+    op.dst = b->d_ord;
+    op.width = cnt_bytes / sizeof(unsigned int);
+    op.pitch = cnt_bytes;
+    cudaGraphNode_t deps[2];
+    int ndeps = 0;
     if ((e = cudaGraphCreate(&b->graph, 0)) != cudaSuccess ||
-        (e = cudaGraphAddMemsetNode(&mnode, b->graph, nullptr, 0, &mp)) != cudaSuccess ||
-        (e = cudaGraphAddKernelNode(&b->knode, b->graph, &mnode, 1, &kp)) != cudaSuccess ||
+        (e = cudaGraphAddMemsetNode(&mnode, b->graph, nullptr, 0, &mp)) != cudaSuccess) {
+      batch_drop_graph(b);
+      return cuda_fail(e, "batch graph build");
+    }
+    deps[ndeps++] = mnode;
+    if (ordered &&
+        ((e = cudaGraphAddMemsetNode(&onode, b->graph, nullptr, 0, &op)) != cudaSuccess ||
+         (e = cudaGraphAddKernelNode(&b->cnode, b->graph, &onode, 1, &cp)) != cudaSuccess ||
+         (e = cudaGraphAddKernelNode(&b->snode, b->graph, &b->cnode, 1, &sp)) != cudaSuccess)) {
+      batch_drop_graph(b);
+      return cuda_fail(e, "batch graph build (ordering)");
+    }
+    if (ordered) deps[ndeps++] = b->snode;
+    if ((e = cudaGraphAddKernelNode(&b->knode, b->graph, deps, ndeps, &kp)) != cudaSuccess ||
         (e = cudaGraphInstantiate(&b->exec, b->graph, 0)) != cudaSuccess) {
       batch_drop_graph(b);
       return cuda_fail(e, "batch graph build");
     }
     b->g_E = E; b->g_wpb = wpb; b->g_asmem = asmem; b->g_grid = grid; b->g_smem = smem;
+    b->g_ordered = ordered ? 1 : 0;
+    b->g_ordbuf = b->d_ord;
+    b->g_ogrid = ogrid;
+    b->g_sgrid = sgrid;
   } else {
-    cudaKernelNodeParams kp;
-    memset(&kp, 0, sizeof kp);
-    kp.func = const_cast<void *>(batch_kernel(E, asmem));
-    kp.gridDim = dim3(grid);
-    kp.blockDim = dim3(wpb * 32);
-    kp.sharedMemBytes = (unsigned)smem;
-    kp.kernelParams = kparams;
-    if ((e = cudaGraphExecKernelNodeSetParams(b->exec, b->knode, &kp)) != cudaSuccess)
+    if ((e = cudaGraphExecKernelNodeSetParams(b->exec, b->knode, &kp)) != cudaSuccess ||
+        (ordered && ((e = cudaGraphExecKernelNodeSetParams(b->exec, b->cnode, &cp)) != cudaSuccess ||
+                     (e = cudaGraphExecKernelNodeSetParams(b->exec, b->snode, &sp)) != cudaSuccess)))
       return cuda_fail(e, "batch graph update");
   }
   if ((e = cudaGraphLaunch(b->exec, b->stream)) != cudaSuccess)

@@ -96,6 +96,44 @@ def test_batch_full_size_all_cells(cuda):
     batch.close()
 
 
+def test_batch_ordering_is_bitwise_neutral(cuda):
+    """Hardest-first ordering of each mechanism's cells (the default) changes
+    which cells share a warp, never a cell's result: bitwise the index-order
+    outputs, at full size, for every launch configuration kind, across graph
+    replays with new pointers and with cell counts that change (the ordering
+    scratch grows and the graph is rebuilt)."""
+    import torch
+    camp, cbs, tol, maxit, solvers, A, b = _setup(cuda, None)
+    batch = camp.Batch(solvers)
+    for cfg in ((0, 0, 1), (5, 8, 0)):
+        batch.set_config(*cfg)
+        batch.set_ordering(0)
+        ref = [[t.clone() for t in o] for o in batch.solve(A, b, tol, maxit)]
+        batch.set_ordering(1)
+        for rep in range(2):
+            out = batch.solve(A, b, tol, maxit)
+            torch.cuda.synchronize()
+            for r, o in zip(ref, out):
+                for x, y in zip(r, o):
+                    assert torch.equal(x, y), (cfg, rep)
+        # fewer cells, then more than ever before
+        part = [a[: a.shape[0] // 3] for a in A], [v[: v.shape[0] // 3] for v in b]
+        out = batch.solve(part[0], part[1], tol, maxit)
+        torch.cuda.synchronize()
+        for r, o in zip(ref, out):
+            for x, y in zip(r, o):
+                assert torch.equal(x[: y.shape[0]], y), cfg
+        big = [torch.cat([a, a]) for a in A], [torch.cat([v, v]) for v in b]
+        out = batch.solve(big[0], big[1], tol, maxit)
+        torch.cuda.synchronize()
+        for r, o in zip(ref, out):
+            for x, y in zip(r, o):
+                assert torch.equal(torch.cat([x, x]), y), cfg
+    with pytest.raises(camp.CampError):
+        batch.set_ordering(2)
+    batch.close()
+
+
 def test_tuner_picks_a_valid_config(cuda, tmp_path, monkeypatch):
     import torch
     from paper_2405_17363_gb300 import tune
