@@ -573,7 +573,8 @@ def run_uneven_case(args):
     from paper_2405_17363_gb300 import camp
     dev = torch.device("cuda", 0)
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
-    res = time_uneven(camp, dev, flush, torch.cuda.current_stream(), steps=args.steps)
+    res = time_uneven(camp, dev, flush, torch.cuda.current_stream(), steps=args.steps,
+                      tune=not args.no_tune)
     print(json.dumps({"case": "uneven", **res}), flush=True)
 
 
@@ -665,6 +666,9 @@ def main():
                     help="cell ordering: 0 index order, 1 hardest first ordered inside the "
                          "solve launch, 2 hardest first by a separate pass (default: the "
                          "library's)")
+    ap.add_argument("--no-tune", action="store_true",
+                    help="--case uneven: keep the batch's automatic launch configuration "
+                         "(no autotuning launches, e.g. for profiling)")
     ap.add_argument("--skip-extras", action="store_true",
                     help="time the device solve only (no e2e, CPU baseline or mixed side run)")
     args = ap.parse_args()
