@@ -38,11 +38,25 @@ DEFAULT_ORDERING = 1  # the library default of camp_solver_set_ordering
 HBM_PEAK_FALLBACK = 6800.0
 # FP64 pipe: 2 DFMA per clock per SM (4 flops) x 152 SMs x 2.07 GHz max clock
 FP64_PEAK_GFLOPS = 4 * 152 * 2.07
-# DRAM bytes (read + write) per launch of the headline kernel from one ncu
-# capture (dram__bytes_read.sum + dram__bytes_write.sum), valid only for the
-# library revision it was taken on; any other revision reports null.
-TRAFFIC_BYTES = {"campsolve 0.10 (sm_103a)": 51.665e6,
-                 "campsolve 0.11 (sm_103a)": 51.747e6}
+# The committed ncu summary of the headline kernel states its DRAM bytes
+# (read + write) per launch and the library revision they were taken on.
+TRAFFIC_PROFILE = os.path.join(ROOT, "profiles", "warp_bicgstab_80sp_10k.md")
+
+
+def measured_traffic(version):
+    """DRAM bytes per launch of the headline kernel from the committed ncu
+    summary (dram__bytes_read.sum + dram__bytes_write.sum of one capture), or
+    None if the summary was taken on another library revision."""
+    import re
+    try:
+        with open(TRAFFIC_PROFILE) as f:
+            for line in f:
+                m = re.match(r"traffic_bytes_per_launch: (\d+) \(library `(.+)`\)", line.strip())
+                if m and m.group(2) == version:
+                    return float(m.group(1))
+    except OSError:
+        pass
+    return None
 
 
 def peaks():
@@ -793,7 +807,7 @@ def main():
             "roofline": {"bound": "alu", "achieved": flops / kernel_s / 1e9,
                          "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s",
                          "frac": flops / kernel_s / 1e9 / FP64_PEAK_GFLOPS,
-                         "traffic": TRAFFIC_BYTES.get(camp.camp_version())
+                         "traffic": measured_traffic(camp.camp_version())
                          if args.arrangement == "auto" and args.mode == "fp64" else None,
                          "peak_source": "FP64 pipe 4 flop/clk/SM x 152 SMs x 2.07 GHz"},
             "hbm_roofline": {"bound": "hbm", "achieved": nbytes / kernel_s / 1e9,

@@ -237,3 +237,17 @@ def test_spmv_schedule_spreads_gathers_over_banks(lib, wid):
                 total += max(len(v) for v in per_bank.values())
         mean = total / (2 * L.value)
         assert mean <= (1.3 if lc <= 16 else 1.6), (m.n, lc, mean)
+
+
+def test_committed_traffic_figure_matches_the_library_revision(lib):
+    """bench.py reports the headline kernel's DRAM traffic from the committed
+    ncu summary only when it was captured on this library revision: the
+    summary must name the revision the library reports."""
+    import sys
+    sys.path.insert(0, ROOT)
+    import bench
+    lib.camp_version.restype = ctypes.c_char_p
+    version = lib.camp_version().decode()
+    traffic = bench.measured_traffic(version)
+    assert traffic is not None and 40e6 < traffic < 80e6, (version, traffic)
+    assert bench.measured_traffic("campsolve 0.0 (none)") is None
