@@ -178,27 +178,42 @@ __device__ __forceinline__ void seg_spmv_gather(const SchedWord *__restrict__ sc
   }, gs, os);
 }
 
-// Coalesced read of one cell's A row (CSR order, lane sl reads entries
-// sl, sl + Lc, ...) handed to put(slot, value) with the slot from the dst map.
-// The loads are issued kStageBatch at a time before any store, so a lane
-// waits for memory once per batch rather than once per entry.
-constexpr int kStageBatch = 16;
+// Coalesced, vectorised read of one cell's A row (CSR order), handed to
+// put(slot, value) with the slot from the dst map.  The row is read in
+// 16-byte pairs from its first 16-byte boundary (lane sl reads pairs sl,
+// sl + Lc, ...); an entry before that boundary and an odd entry at the end
+// are read alone by lane 0.  The loads of kStagePairs pairs are issued before
+// any store, so a lane waits for memory once per batch rather than once per
+// entry.
+constexpr int kStagePairs = 8;
 template <class Put>
 __device__ __forceinline__ void stage_scatter(const double *__restrict__ Ac,
                                               const int *__restrict__ dst, int nnz,
                                               int sl, int Lc, bool live, Put put) {
-  for (int k0 = sl; k0 < nnz; k0 += kStageBatch * Lc) {
-    double v[kStageBatch];
-    int d[kStageBatch];
+  const int h = (int)((reinterpret_cast<size_t>(Ac) >> 3) & 1);  // entries before the boundary
+  const int np = (nnz - h) >> 1;                                  // whole pairs
+  const double2 *A2 = reinterpret_cast<const double2 *>(Ac + h);
+  const int *d2 = dst + h;
+  for (int p0 = sl; p0 < np; p0 += kStagePairs * Lc) {
+    double2 v[kStagePairs];
+    int d[2 * kStagePairs];
 #pragma unroll
-    for (int u = 0; u < kStageBatch; ++u) {
-      const int k = k0 + u * Lc;
-      d[u] = k < nnz ? __ldg(dst + k) : -1;
-      v[u] = (live && k < nnz) ? __ldg(Ac + k) : 0.0;
+    for (int u = 0; u < kStagePairs; ++u) {
+      const int p = p0 + u * Lc;
+      const bool in = p < np;
+      d[2 * u] = in ? __ldg(d2 + 2 * p) : -1;
+      d[2 * u + 1] = in ? __ldg(d2 + 2 * p + 1) : -1;
+      v[u] = (live && in) ? __ldg(A2 + p) : make_double2(0.0, 0.0);
     }
 #pragma unroll
-    for (int u = 0; u < kStageBatch; ++u)
-      if (d[u] >= 0) put(d[u], v[u]);
+    for (int u = 0; u < kStagePairs; ++u) {
+      if (d[2 * u] >= 0) put(d[2 * u], v[u].x);
+      if (d[2 * u + 1] >= 0) put(d[2 * u + 1], v[u].y);
+    }
+  }
+  if (sl == 0) {
+    if (h) put(__ldg(dst), live ? __ldg(Ac) : 0.0);
+    if ((nnz - h) & 1) put(__ldg(dst + nnz - 1), live ? __ldg(Ac + nnz - 1) : 0.0);
   }
 }
 
