@@ -581,6 +581,21 @@ def run_step_case(args):
     print(json.dumps({"case": args.case, **res}), flush=True)
 
 
+def run_side_case(args):
+    """--case cfg4 / --case adjoint: the 150-species mixed-precision block or
+    the adjoint block alone (for profiling)."""
+    import torch
+    from paper_2405_17363_gb300 import camp
+    dev = torch.device("cuda", 0)
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+    st = torch.cuda.current_stream()
+    if args.case == "cfg4":
+        res = time_cfg4(camp, dev, flush, st, steps=args.steps)
+    else:
+        res = time_adjoint(camp, dev, flush, st, steps=args.steps)
+    print(json.dumps({"case": args.case, **res}), flush=True)
+
+
 def run_uneven_case(args):
     """--case uneven: the persistent batch alone, timed as the step."""
     import torch
@@ -671,7 +686,7 @@ def main():
                     help="fp64: plain FP64 solve (the headline); mixed: FP32-inner refinement")
     ap.add_argument("--case", default="headline",
                     choices=["headline", "uneven", "arrangements", "variability", "fused",
-                             "newton"],
+                             "newton", "cfg4", "adjoint"],
                     help="headline: the 80-species 10k-cell FP64 solve; uneven: time the "
                          "persistent multi-mechanism batch as the step; fused / newton: the "
                          "in-kernel assembly or the device Newton corrector alone (for "
@@ -703,6 +718,8 @@ def main():
         return run_variability_case(args)
     if args.case in ("fused", "newton"):
         return run_step_case(args)
+    if args.case in ("cfg4", "adjoint"):
+        return run_side_case(args)
 
     import torch
     import torch.distributed as dist

@@ -258,6 +258,7 @@ struct MixedArgs {
   int max_sweeps;
   float tol_in;
   int maxit_in;
+  int a64_smem;   // 1: FP64 A staged in shared memory; 0: read through L1 from A
   // dynamic group queue and difficulty ordering, as in WarpArgs
   unsigned int *queue;
   const int *order;

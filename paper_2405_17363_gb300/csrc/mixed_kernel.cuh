@@ -6,8 +6,12 @@
 // pipe only sees the residual products, norms and updates; the inner
 // iterations run on the FP32 pipe.
 //
-// Shared memory per cell: A in FP64 [segA] and FP32 [segA], the FP64 product
-// input/output vectors [segV each] and three FP32 vectors [segV each].
+// Shared memory per cell: A in FP32 [segA] and, when a.a64_smem is set, in
+// FP64 [segA] (otherwise the FP64 residual product reads A through L1 from
+// the cell's row in global memory, which the staging has just brought into
+// L2: it runs two or three times per cell, against tens of FP32 products, and
+// the smaller footprint lets more warps run), the FP64 product input/output
+// vectors [segV each] and three FP32 vectors [segV each].
 #pragma once
 #include "warp_common.cuh"
 
@@ -26,12 +30,13 @@ __device__ __forceinline__ void mixed_body(const MixedArgs &a) {
   const int seg = LC ? lane / LC : lane >> a.log2Lc;
   const int sl = lane & (Lc - 1);
   const int n = a.n, nnz = a.nnz;
-  // bytes per cell: 12 segA + 16 segV + 12 segV (FP64 A, FP32 A, 2 FP64 + 3 FP32 vectors)
-  const size_t cellBytes = (size_t)12 * a.segA + (size_t)28 * a.segV;
+  // bytes per cell: (12 or 4) segA + 16 segV + 12 segV (FP64 A when staged,
+  // FP32 A, 2 FP64 + 3 FP32 vectors)
+  const size_t cellBytes = (size_t)(a.a64_smem ? 12 : 4) * a.segA + (size_t)28 * a.segV;
   unsigned char *wb = smem_raw + sched_smem_bytes(nsch) +
                       ((size_t)warp * a.k + seg) * cellBytes;
   double *As = reinterpret_cast<double *>(wb);
-  double *g64 = As + a.segA;
+  double *g64 = As + (a.a64_smem ? a.segA : 0);
   double *o64 = g64 + a.segV;
   float *As32 = reinterpret_cast<float *>(o64 + a.segV);
   float *g32 = As32 + a.segA;
@@ -57,15 +62,17 @@ __device__ __forceinline__ void mixed_body(const MixedArgs &a) {
                       ? (int)min((unsigned)(__ldcg(a.order + pos) - (a.ord_ws ? 1 : 0)),
                                  (unsigned)a.cells - 1u)
                       : pos;
-    {  // stage A in slot order, FP64 and its FP32 rounding
-      const double *Ac = a.A + (size_t)(has ? c : 0) * nnz;
+    const double *Ac = a.A + (size_t)(has ? c : 0) * nnz;
+    if (a.a64_smem) {  // stage A in slot order, FP64 and its FP32 rounding
       stage_scatter(Ac, a.dst, nnz, sl, Lc, has, [&](int t, double v) {
         As[t] = v;
         As32[t] = d2f_rn(v);
       });
       zero_padding(As, a.padfrom, a.L, Lc, sl);
-      zero_padding(As32, a.padfrom, a.L, Lc, sl);
+    } else {  // the FP32 rounding only
+      stage_scatter(Ac, a.dst, nnz, sl, Lc, has, [&](int t, double v) { As32[t] = d2f_rn(v); });
     }
+    zero_padding(As32, a.padfrom, a.L, Lc, sl);
     __syncwarp();
     double xv[E];
     float dinv[E];
@@ -103,7 +110,8 @@ __device__ __forceinline__ void mixed_body(const MixedArgs &a) {
 #pragma unroll
         for (int e = 0; e < E; ++e) g64[sl + e * Lc] = xv[e];
         __syncwarp();
-        seg_spmv(sch, a.L, Lc, As + sl, g64, o64);
+        if (a.a64_smem) seg_spmv(sch, a.L, Lc, As + sl, g64, o64);
+        else seg_spmv_gather(sch, a.src + sl, a.L, Lc, Ac, g64, o64);
         __syncwarp();
       }
       double rr[1] = {0.0};

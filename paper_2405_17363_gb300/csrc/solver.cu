@@ -406,13 +406,41 @@ size_t warp_smem(const View &v, int Lc, int L, int wpb, int *segA, int *segV,
   return sch + (size_t)wpb * k * (size_t)*segStride * 8;
 }
 
-size_t mixed_smem(const View &v, int Lc, int L, int wpb, int *segA, int *segV) {
+// Warps per block of an automatic warp-packed launch: the most resident
+// warps per SM (the CTA's schedule copy and its warps' cell regions must pack
+// into the SM's shared memory; occ gives the CTAs per SM of the kernel), 4
+// unless another count fits more.  Fills the shared-memory layout.
+typedef cudaError_t (*OccFn)(int E, int wpb, size_t smem, int *blocks);
+cudaError_t pick_warps_per_block(const View &v, int Lc, int L, int E, int extra_vectors,
+                                 size_t optin, OccFn occ_fn, int *wpb, size_t *smem,
+                                 int *segA, int *segV, int *segStride) {
+  int best = -1;
+  for (int w : {4, 8, 6, 5, 3, 2, 1}) {
+    int sa = 0, sv = 0, ss = 0, occ = 0;
+    const size_t sm = warp_smem(v, Lc, L, w, &sa, &sv, &ss, extra_vectors);
+    if (sm > optin) continue;
+    const cudaError_t e = occ_fn(E, w, sm, &occ);
+    if (e != cudaSuccess) return e;
+    if (occ * w > best) {
+      best = occ * w;
+      *wpb = w;
+    }
+  }
+  if (best < 0) {
+    *smem = optin + 1;  // does not fit even with one warp
+    return cudaSuccess;
+  }
+  *smem = warp_smem(v, Lc, L, *wpb, segA, segV, segStride, extra_vectors);
+  return cudaSuccess;
+}
+
+size_t mixed_smem(const View &v, int Lc, int L, int wpb, int *segA, int *segV, bool a64_smem) {
   const int k = 32 / Lc;
   const int E = (v.n + Lc - 1) / Lc;
   *segA = (L * Lc + 1) & ~1;  // A in slot order
   *segV = ((E * Lc + 1) + 1) & ~1;
   const size_t sch = sched_smem_bytes(L * Lc);
-  return sch + (size_t)wpb * k * ((size_t)12 * *segA + (size_t)28 * *segV);
+  return sch + (size_t)wpb * k * ((size_t)(a64_smem ? 12 : 4) * *segA + (size_t)28 * *segV);
 }
 
 // Automatic arrangement: the most cells per warp (fewest lanes per cell) that
@@ -668,6 +696,10 @@ camp_status do_solve(camp_solver_t h, int cells, const double *A_vals,
     }
     if (smem > h->smem_optin)
       return fail(CAMP_EUNSUPPORTED, "cell does not fit in shared memory (%zu bytes)", smem);
+    if (h->wpb == 0 &&
+        (e = pick_warps_per_block(v, Lc, S->L, E, 0, h->smem_optin, warp_occupancy, &wpb, &smem,
+                                  &segA, &segV, &segStride)) != cudaSuccess)
+      return cuda_fail(e, "occupancy");
     WarpArgs a = {};
     a.cells = cells; a.n = v.n; a.nnz = v.nnz;
     a.Lc = Lc; a.log2Lc = ilog2(Lc); a.k = 32 / Lc; a.L = S->L;
@@ -1220,8 +1252,8 @@ cudaError_t mech_terms(Mechanism &mech, int Lc, const Schedule &S, MechTerms **o
 
 // Launch arguments shared by the fused assembly and the Newton launches;
 // extra_vectors = shared vectors per cell beyond the solve's own.  Returns CAMP_OK or the error.
-static camp_status fused_args(camp_solver_t h, int cells, int extra_vectors, WarpArgs *pa, int *pE,
-                              int *pwpb, size_t *psmem) {
+static camp_status fused_args(camp_solver_t h, int cells, int extra_vectors, OccFn occ_fn,
+                              WarpArgs *pa, int *pE, int *pwpb, size_t *psmem) {
   cudaError_t e = cudaSetDevice(h->device);
   if (e != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
   View &v = h->fwd;
@@ -1240,6 +1272,10 @@ static camp_status fused_args(camp_solver_t h, int cells, int extra_vectors, War
   while (smem > h->smem_optin && wpb > 1)
     smem = warp_smem(v, Lc, S->L, --wpb, &segA, &segV, &segStride, extra_vectors);
   if (smem > h->smem_optin) return fail(CAMP_EUNSUPPORTED, "cell does not fit in shared memory");
+  if (h->wpb == 0 &&
+      (e = pick_warps_per_block(v, Lc, S->L, E, extra_vectors, h->smem_optin, occ_fn, &wpb, &smem,
+                                &segA, &segV, &segStride)) != cudaSuccess)
+    return cuda_fail(e, "occupancy");
   WarpArgs a = {};
   a.cells = cells; a.n = v.n; a.nnz = v.nnz;
   a.Lc = Lc; a.log2Lc = ilog2(Lc); a.k = 32 / Lc; a.L = S->L;
@@ -1273,7 +1309,7 @@ camp_status camp_solver_assemble_solve(camp_solver_t h, int cells,
   WarpArgs a;
   int E = 0, wpb = 0;
   size_t smem = 0;
-  camp_status rc = fused_args(h, cells, 0, &a, &E, &wpb, &smem);
+  camp_status rc = fused_args(h, cells, 0, assemble_occupancy, &a, &E, &wpb, &smem);
   if (rc != CAMP_OK) return rc;
   a.A = nullptr; a.b = b; a.x = x; a.iters = iters_out; a.resid = resid_out;
   a.status = status_out;
@@ -1310,7 +1346,7 @@ camp_status camp_solver_newton_solve(camp_solver_t h, int cells,
   WarpArgs a;
   int E = 0, wpb = 0;
   size_t smem = 0;
-  camp_status rc = fused_args(h, cells, 1, &a, &E, &wpb, &smem);
+  camp_status rc = fused_args(h, cells, 1, newton_occupancy, &a, &E, &wpb, &smem);
   if (rc != CAMP_OK) return rc;
   a.A = nullptr; a.b = a_hist; a.x = y; a.iters = lin_iters_out; a.resid = resid_out;
   a.status = status_out;
@@ -1351,11 +1387,27 @@ camp_status camp_solver_solve_mixed(camp_solver_t h, int cells,
   if (E > kMaxE) return fail(CAMP_EUNSUPPORTED, "n=%d too large for %d lanes per cell", v.n, Lc);
   Schedule *S = nullptr;
   if ((e = view_schedule(v, Lc, &S)) != cudaSuccess) return cuda_fail(e, "schedule upload");
-  int wpb = h->wpb > 0 ? h->wpb : 4;
-  int segA = 0, segV = 0;
-  size_t smem = mixed_smem(v, Lc, S->L, wpb, &segA, &segV);
-  while (smem > h->smem_optin && wpb > 1) smem = mixed_smem(v, Lc, S->L, --wpb, &segA, &segV);
-  if (smem > h->smem_optin) return fail(CAMP_EUNSUPPORTED, "cell does not fit in shared memory");
+  // FP64 A in shared memory unless that costs resident warps (then the
+  // outer residual product reads it through L1)
+  const int wpb0 = h->wpb > 0 ? h->wpb : 4;
+  int wpb = wpb0, segA = 0, segV = 0, best_warps = -1;
+  bool a64 = true;
+  size_t smem = 0;
+  for (int s64 = 1; s64 >= 0; --s64) {
+    int w = wpb0;
+    size_t sm = mixed_smem(v, Lc, S->L, w, &segA, &segV, s64 != 0);
+    while (sm > h->smem_optin && w > 1) sm = mixed_smem(v, Lc, S->L, --w, &segA, &segV, s64 != 0);
+    if (sm > h->smem_optin) continue;
+    int occ = 0;
+    if ((e = mixed_occupancy(E, w, sm, &occ)) != cudaSuccess) return cuda_fail(e, "occupancy");
+    if (occ * w > best_warps) {  // resident warps per SM; a tie keeps the staged FP64 A
+      best_warps = occ * w;
+      a64 = s64 != 0;
+      wpb = w;
+    }
+  }
+  if (best_warps < 0) return fail(CAMP_EUNSUPPORTED, "cell does not fit in shared memory");
+  smem = mixed_smem(v, Lc, S->L, wpb, &segA, &segV, a64);
   MixedArgs a = {};
   a.cells = cells; a.n = v.n; a.nnz = v.nnz;
   a.Lc = Lc; a.log2Lc = ilog2(Lc); a.k = 32 / Lc; a.L = S->L;
@@ -1365,6 +1417,7 @@ camp_status camp_solver_solve_mixed(camp_solver_t h, int cells,
   a.dst = S->d_dst; a.padfrom = S->d_padfrom; a.dslot = S->d_dslot;
   a.tol = tol; a.max_sweeps = max_sweeps; a.tol_in = (float)tol_inner;
   a.maxit_in = maxit_inner;
+  a.a64_smem = a64 ? 1 : 0;
   a.queue = h->d_queue;  // the handle's own stream: queue pair 0
   // Ordering pays here only by pairing: with one cell per warp (the automatic
   // choice above 48 species) its prologue costs more than hardest-first saves
@@ -1602,6 +1655,20 @@ camp_status camp_batch_solve(camp_batch_t b, const int *cells,
   size_t smem = (size_t)wpb * warp_doubles * 8;
   while (smem > b->smem_optin && wpb > 1) smem = (size_t)(--wpb) * warp_doubles * 8;
   if (smem > b->smem_optin) return fail(CAMP_EUNSUPPORTED, "a warp's cells do not fit in shared memory");
+  if (b->wpb == 0) {  // the most resident warps per SM, 4 unless another count fits more
+    int best = -1;
+    for (int w : {4, 8, 6, 5, 3, 2, 1}) {
+      const size_t sm = (size_t)w * warp_doubles * 8;
+      int o = 0;
+      if (sm > b->smem_optin) continue;
+      if ((e = batch_prepare(E, asmem, w, sm, &o)) != cudaSuccess) return cuda_fail(e, "batch occupancy");
+      if (o * w > best) {
+        best = o * w;
+        wpb = w;
+      }
+    }
+    smem = (size_t)wpb * warp_doubles * 8;
+  }
   int occ = 0;
   if ((e = batch_prepare(E, asmem, wpb, smem, &occ)) != cudaSuccess) return cuda_fail(e, "batch occupancy");
   if (occ < 1) occ = 1;
