@@ -92,17 +92,15 @@ struct LaneRows<E, false> {
 // A d = -G(y) through stage_and_solve, then y += d; converged when
 // ||d|| <= newton_tol ||y||.  Status 0 converged, 1 iterations exhausted,
 // 2 linear solve failed, 3 non-finite; iters = BiCGSTAB iterations summed.
+// The iterate lives in the caller's x (it holds the guess on entry and the
+// solution on return): read at the start of an iteration and written back
+// after the update, so no register holds it across the linear solve.
 template <int E, class Solve>
 __device__ __forceinline__ void newton_loop(const WarpArgs &a, bool has, bool &live, int c,
                                             int sl, int Lc, int n, double *o1, double *o2,
                                             double *nrh, double (&xv)[E], int &st, int &it,
                                             double &resid, Solve &stage_and_solve) {
-  double y[E];
-#pragma unroll
-  for (int e = 0; e < E; ++e) {
-    const int i = sl + e * Lc;
-    y[e] = (has && i < n) ? a.x[(size_t)c * n + i] : 0.0;
-  }
+  double *yc = a.x + (size_t)c * n;  // the iterate (c is in range whenever has)
   const double gam = has ? __ldg(a.gamma + c) : 0.0;
   const double nt2 = a.newton_tol * a.newton_tol;
   const bool any = a.max_newton > 0;
@@ -114,8 +112,9 @@ __device__ __forceinline__ void newton_loop(const WarpArgs &a, bool has, bool &l
     // lane adds the terms of its own rows)
 #pragma unroll
     for (int e = 0; e < E; ++e) {
-      o2[sl + e * Lc] = y[e];
-      o1[sl + e * Lc] = 0.0;
+      const int i = sl + e * Lc;
+      o2[i] = (has && i < n) ? yc[i] : 0.0;
+      o1[i] = 0.0;
     }
     __syncwarp();
     const double *rv = a.rval + sl;
@@ -133,7 +132,7 @@ __device__ __forceinline__ void newton_loop(const WarpArgs &a, bool has, bool &l
     for (int e = 0; e < E; ++e) {
       const int i = sl + e * Lc;
       const double ai = (act && i < n) ? __ldg(a.b + (size_t)c * n + i) : 0.0;
-      nrh[i] = ai - fma(-gam, o1[i], y[e]);
+      nrh[i] = ai - fma(-gam, o1[i], o2[i]);
     }
     __syncwarp();
     live = act;
@@ -142,9 +141,14 @@ __device__ __forceinline__ void newton_loop(const WarpArgs &a, bool has, bool &l
     double d2 = 0.0, y2 = 0.0;
 #pragma unroll
     for (int e = 0; e < E; ++e) {
-      if (ok) y[e] += xv[e];
+      const int i = sl + e * Lc;
+      double ye = (has && i < n) ? yc[i] : 0.0;
+      if (ok) {
+        ye += xv[e];
+        if (i < n) yc[i] = ye;
+      }
       d2 = fma(xv[e], xv[e], d2);
-      y2 = fma(y[e], y[e], y2);
+      y2 = fma(ye, ye, y2);
     }
     d2 = seg_sum_exact(d2, Lc);
     y2 = seg_sum_exact(y2, Lc);
@@ -172,19 +176,12 @@ __device__ __forceinline__ void newton_loop(const WarpArgs &a, bool has, bool &l
       }
     }
   }
-  if (has) {
-#pragma unroll
-    for (int e = 0; e < E; ++e) {
-      const int i = sl + e * Lc;
-      if (i < n) a.x[(size_t)c * n + i] = y[e];
-    }
-    if (sl == 0) {
-      a.newton_iters[c] = nit;
-      a.iters[c] = lin;
-      a.upd[c] = upd;
-      a.resid[c] = lres;
-      if (a.status) a.status[c] = nst;
-    }
+  if (has && sl == 0) {
+    a.newton_iters[c] = nit;
+    a.iters[c] = lin;
+    a.upd[c] = upd;
+    a.resid[c] = lres;
+    if (a.status) a.status[c] = nst;
   }
   __syncwarp();
 }
