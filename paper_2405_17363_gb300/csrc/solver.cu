@@ -202,6 +202,9 @@ struct Schedule {
   std::vector<int> dslot;        // [n]
   std::vector<int> dst;          // [nnz] slot of each A entry (forward order)
   std::vector<int> padfrom;      // [Lc] first padding slot of each lane
+  // automatic warps per block, found once per kernel kind (0: not yet):
+  // plain solve, fused assembly, Newton corrector
+  int auto_wpb[3] = {0, 0, 0};
   SchedWord *d_words = nullptr;
   int *d_src = nullptr, *d_dslot = nullptr, *d_dst = nullptr, *d_padfrom = nullptr;
 };
@@ -412,8 +415,13 @@ size_t warp_smem(const View &v, int Lc, int L, int wpb, int *segA, int *segV,
 // unless another count fits more.  Fills the shared-memory layout.
 typedef cudaError_t (*OccFn)(int E, int wpb, size_t smem, int *blocks);
 cudaError_t pick_warps_per_block(const View &v, int Lc, int L, int E, int extra_vectors,
-                                 size_t optin, OccFn occ_fn, int *wpb, size_t *smem,
+                                 size_t optin, OccFn occ_fn, int *cache, int *wpb, size_t *smem,
                                  int *segA, int *segV, int *segStride) {
+  if (*cache > 0) {
+    *wpb = *cache;
+    *smem = warp_smem(v, Lc, L, *wpb, segA, segV, segStride, extra_vectors);
+    return cudaSuccess;
+  }
   int best = -1;
   for (int w : {4, 8, 6, 5, 3, 2, 1}) {
     int sa = 0, sv = 0, ss = 0, occ = 0;
@@ -430,6 +438,7 @@ cudaError_t pick_warps_per_block(const View &v, int Lc, int L, int E, int extra_
     *smem = optin + 1;  // does not fit even with one warp
     return cudaSuccess;
   }
+  *cache = *wpb;
   *smem = warp_smem(v, Lc, L, *wpb, segA, segV, segStride, extra_vectors);
   return cudaSuccess;
 }
@@ -697,8 +706,9 @@ camp_status do_solve(camp_solver_t h, int cells, const double *A_vals,
     if (smem > h->smem_optin)
       return fail(CAMP_EUNSUPPORTED, "cell does not fit in shared memory (%zu bytes)", smem);
     if (h->wpb == 0 &&
-        (e = pick_warps_per_block(v, Lc, S->L, E, 0, h->smem_optin, warp_occupancy, &wpb, &smem,
-                                  &segA, &segV, &segStride)) != cudaSuccess)
+        (e = pick_warps_per_block(v, Lc, S->L, E, 0, h->smem_optin, warp_occupancy,
+                                  &S->auto_wpb[0], &wpb, &smem, &segA, &segV, &segStride)) !=
+            cudaSuccess)
       return cuda_fail(e, "occupancy");
     WarpArgs a = {};
     a.cells = cells; a.n = v.n; a.nnz = v.nnz;
@@ -1273,8 +1283,9 @@ static camp_status fused_args(camp_solver_t h, int cells, int extra_vectors, Occ
     smem = warp_smem(v, Lc, S->L, --wpb, &segA, &segV, &segStride, extra_vectors);
   if (smem > h->smem_optin) return fail(CAMP_EUNSUPPORTED, "cell does not fit in shared memory");
   if (h->wpb == 0 &&
-      (e = pick_warps_per_block(v, Lc, S->L, E, extra_vectors, h->smem_optin, occ_fn, &wpb, &smem,
-                                &segA, &segV, &segStride)) != cudaSuccess)
+      (e = pick_warps_per_block(v, Lc, S->L, E, extra_vectors, h->smem_optin, occ_fn,
+                                &S->auto_wpb[extra_vectors ? 2 : 1], &wpb, &smem, &segA, &segV,
+                                &segStride)) != cudaSuccess)
     return cuda_fail(e, "occupancy");
   WarpArgs a = {};
   a.cells = cells; a.n = v.n; a.nnz = v.nnz;
