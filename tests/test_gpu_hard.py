@@ -116,3 +116,92 @@ def test_residual_replacement_well_conditioned_strict(camp, cuda):
     assert restarted.size >= 10
     parity.compare(m, cb.A_vals, cb.b, tol, gpu, orc, "tol 1e-15")
     assert np.all(gpu["status"][restarted] == 0)
+
+
+def test_hard_regime_transposed_all_cells(camp, cuda, hard):
+    """The adjoint's transposed solve (A^T lambda = w through the transposed
+    pattern) on the hard cells (mean 74 iterations, a few cells at the cap),
+    every cell against the oracle on the transposed CSR."""
+    cb = hard
+    m = cb.mech
+    tol, maxit = 1e-10, 500
+    rpt, cit, src = oracle.transpose_pattern(m.row_ptr, m.col_idx)
+    AT = np.ascontiguousarray(cb.A_vals[:, src])
+    mT = synth.Mechanism(n=m.n, R=0, reactants=None, products=None, k=None,
+                         row_ptr=rpt, col_idx=cit)
+    import torch
+    s = camp.Solver(m.row_ptr, m.col_idx)
+    x, it, res, st = s.solve(torch.as_tensor(cb.A_vals, device=cuda),
+                             torch.as_tensor(cb.b, device=cuda), tol, maxit, transpose=True)
+    torch.cuda.synchronize()
+    gpu = dict(x=x.cpu().numpy(), iters=it.cpu().numpy(), resid=res.cpu().numpy(),
+               status=st.cpu().numpy())
+    s.close()
+    orc, pert = _oracles(mT, AT, cb.b, tol, maxit)
+    assert orc["iters"].mean() >= 30
+    res = parity.compare_sensitive(mT, AT, cb.b, tol, maxit, gpu, orc, pert, "hard transposed")
+    print(f"hard transposed: oracle mean iters {orc['iters'].mean():.2f}, gpu "
+          f"{gpu['iters'].mean():.2f}; {res}")
+
+
+def test_hard_regime_persistent_batch(camp, cuda, hard):
+    """The persistent multi-mechanism launch (under its graph, cells ordered
+    hardest first per mechanism) with the hard mechanism next to an easy one:
+    the hard cells against the oracle with the rounding-sensitive bar, the
+    easy cells with the strict bar."""
+    import torch
+    easy = synth.workload(2, cells=3000)[0][0]
+    tol, maxit = 1e-10, 500
+    solvers = [camp.Solver(cb.mech.row_ptr, cb.mech.col_idx) for cb in (hard, easy)]
+    batch = camp.Batch(solvers)
+    out = batch.solve([torch.as_tensor(cb.A_vals, device=cuda) for cb in (hard, easy)],
+                      [torch.as_tensor(cb.b, device=cuda) for cb in (hard, easy)], tol, maxit)
+    torch.cuda.synchronize()
+    got = [dict(x=o[0].cpu().numpy(), iters=o[1].cpu().numpy(), resid=o[2].cpu().numpy(),
+                status=o[3].cpu().numpy()) for o in out]
+    batch.close()
+    for sv in solvers:
+        sv.close()
+    m = hard.mech
+    orc, pert = _oracles(m, hard.A_vals, hard.b, tol, maxit)
+    res = parity.compare_sensitive(m, hard.A_vals, hard.b, tol, maxit, got[0], orc, pert,
+                                   "hard batch")
+    me = easy.mech
+    orc_e = oracle.solve(me.row_ptr, me.col_idx, easy.A_vals, easy.b, tol, maxit, threads=THREADS)
+    parity.compare(me, easy.A_vals, easy.b, tol, got[1], orc_e, "easy batch")
+    print(f"hard batch: {res}")
+
+
+def test_hard_regime_mixed_refinement(camp, cuda, hard):
+    """The FP32-inner refinement on the hard cells (κ up to ~1e7: 3 % of the
+    cells exhaust the 20 outer sweeps): against the refinement oracle with the
+    rounding-sensitive bar, the outer sweeps in the place of iterations (a
+    MAXIT cell has run all 20), and every cell it converges within the 1e-8
+    bar of the FP64 oracle's solution."""
+    import torch
+    cb = hard
+    m = cb.mech
+    tol, sweeps_max = 1e-10, 20
+    s = camp.Solver(m.row_ptr, m.col_idx)
+    x, it, sw, res, st = s.solve_mixed(torch.as_tensor(cb.A_vals, device=cuda),
+                                       torch.as_tensor(cb.b, device=cuda), tol)
+    torch.cuda.synchronize()
+    gpu = dict(x=x.cpu().numpy(), iters=sw.cpu().numpy(), resid=res.cpu().numpy(),
+               status=st.cpu().numpy())
+    s.close()
+
+    def mixed(b):
+        o = oracle.solve_mixed(m.row_ptr, m.col_idx, cb.A_vals, b, tol, threads=THREADS)
+        return dict(o, iters=o["sweeps"])
+    orc = mixed(cb.b)
+    pert = [mixed(parity.perturbed_rhs(cb.b, seed)) for seed in (1, 2)]
+    assert (orc["status"] == 1).sum() >= 50 and (orc["status"] == 0).sum() >= 9000
+    res = parity.compare_sensitive(m, cb.A_vals, cb.b, tol, sweeps_max, gpu, orc, pert,
+                                   "hard mixed")
+    f64 = oracle.solve(m.row_ptr, m.col_idx, cb.A_vals, cb.b, tol, 500, threads=THREADS)
+    conv = (gpu["status"] == 0) & (f64["status"] == 0)
+    err = parity.rel_err(gpu["x"], f64["x"])
+    assert np.all(err[conv] <= parity.REL_TOL), err[conv].max()
+    print(f"hard mixed: statuses gpu {np.bincount(gpu['status'], minlength=4).tolist()} oracle "
+          f"{np.bincount(orc['status'], minlength=4).tolist()}; error vs FP64 oracle max "
+          f"{err[conv].max():.2e} p99 {np.percentile(err[conv], 99):.2e}; {res}")
