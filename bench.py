@@ -509,13 +509,15 @@ def fp64_rate(camp, dev):
     return 2.0 * 4 * n * steps / (ms * 1e-3) / 1e9
 
 
-def time_fused(camp, cb, tol, maxit, flush, stream, dev, steps=200):
+def time_fused(camp, cb, tol, maxit, flush, stream, dev, steps=200, ordering=None):
     """The same cells solved with the matrices assembled in the kernel from
     the concentrations (A = I - gamma J) instead of read from HBM."""
     import torch
     m = cb.mech
     s = camp.Solver(m.row_ptr, m.col_idx)
     s.set_mechanism(m.reactants[:, 0], m.reactants[:, 1], m.products, m.k)
+    if ordering is not None:
+        s.set_ordering(ordering)
     conc = torch.as_tensor(cb.conc, device=dev)
     gam = torch.as_tensor(cb.gamma, device=dev)
     b = torch.as_tensor(cb.b, device=dev)
@@ -531,7 +533,7 @@ def time_fused(camp, cb, tol, maxit, flush, stream, dev, steps=200):
 
 
 def time_newton(camp, cb, flush, stream, dev, steps=50, newton_tol=1e-10, lin_tol=1e-10,
-                lin_maxit=500):
+                lin_maxit=500, ordering=None):
     """The device Newton corrector of the implicit step on the same cells:
     history term a = the cells' concentrations, initial guess y = a; every
     step copies the guess in and runs all Newton iterations of all cells in
@@ -540,6 +542,8 @@ def time_newton(camp, cb, flush, stream, dev, steps=50, newton_tol=1e-10, lin_to
     m = cb.mech
     s = camp.Solver(m.row_ptr, m.col_idx)
     s.set_mechanism(m.reactants[:, 0], m.reactants[:, 1], m.products, m.k)
+    if ordering is not None:
+        s.set_ordering(ordering)
     a = torch.as_tensor(cb.conc, device=dev)
     gam = torch.as_tensor(cb.gamma, device=dev)
     out = s.newton_solve(a, gam, a, newton_tol, 20, lin_tol, lin_maxit)
@@ -575,10 +579,13 @@ def run_step_case(args):
     cbs, tol, maxit = synth.workload(WORKLOAD_ID)
     st = torch.cuda.current_stream()
     if args.case == "fused":
-        res = time_fused(camp, cbs[0], tol, maxit, flush, st, dev, steps=args.steps)
+        res = time_fused(camp, cbs[0], tol, maxit, flush, st, dev, steps=args.steps,
+                         ordering=args.ordering)
     else:
-        res = time_newton(camp, cbs[0], flush, st, dev, steps=args.steps)
-    print(json.dumps({"case": args.case, **res}), flush=True)
+        res = time_newton(camp, cbs[0], flush, st, dev, steps=args.steps,
+                          ordering=args.ordering)
+    ordering = args.ordering if args.ordering is not None else DEFAULT_ORDERING
+    print(json.dumps({"case": args.case, "ordering": ordering, **res}), flush=True)
 
 
 def run_side_case(args):

@@ -157,12 +157,19 @@ camp_status camp_solver_set_arrangement(camp_solver_t h, int arrangement,
  *      normally; camp_solver_get_fault reports it without synchronising.
  *   2: a separate classify and scatter pass (a memset and two small
  *      launches before the solve; about 5 bytes of scratch per cell).
+ * The fused launches (camp_solver_assemble_solve, camp_solver_newton_solve)
+ * have no matrix before a cell is assembled: in modes 1 and 2 they order
+ * inside the launch, as mode 1 does, by |gamma[c]| on the same half-octave
+ * classes (gamma scales every off-identity entry of A = I - gamma J), with
+ * the same bounded waits, time-out report and scratch (8 bytes per cell); a
+ * refused cooperative launch runs them in index order.
  */
 camp_status camp_solver_set_ordering(camp_solver_t h, int ordering);
 
 /*
- * Whether a bounded wait of an in-launch ordering (ordering mode 1, the
- * plain FP64 solve and the FP32-inner refinement) ran out in any launch of
+ * Whether a bounded wait of an in-launch ordering (ordering mode 1 of the
+ * plain FP64 solve and the FP32-inner refinement; modes 1 and 2 of the fused
+ * assembly and Newton launches) ran out in any launch of
  * this handle since the previous query: *ordering_timed_out = 1 (and the
  * report is cleared) or 0.  Reads a host-mapped word the GPU sets; it does
  * not synchronise, so it covers only launches that have completed (call it
@@ -370,7 +377,10 @@ camp_status camp_schedule_build(int n, int nnz, const int *row_ptr,
  * (I - gamma[c] J(conc[c])) x = b[c] exactly as camp_solver_solve_ex would
  * with those matrix values: conc [cells x n], gamma [cells], b, x [cells x n],
  * iters_out, resid_out, status_out (may be NULL) [cells], device pointers.
- * At most 8 rows per lane of the warp arrangement (n <= 256).
+ * At most 8 rows per lane of the warp arrangement (n <= 256).  Cells are
+ * ordered by |gamma| inside the launch (camp_solver_set_ordering); after a
+ * time-out of that ordering every cell carries resid NaN and (status_out
+ * given) CAMP_CELL_INVALID.
  */
 camp_status camp_solver_set_mechanism(camp_solver_t h, int R,
                                       const int *reactant_a,
@@ -403,7 +413,9 @@ camp_status camp_solver_assemble_solve(camp_solver_t h, int cells,
  * resid_out (relative residual of the last linear solve) [cells] are
  * required; status_out [cells] may be NULL: 0 converged, 1 iterations
  * exhausted, 2 linear solve failed (y keeps the iterate before it),
- * 3 non-finite.  All device pointers, written on the handle's stream.
+ * 3 non-finite; CAMP_CELL_INVALID (with resid NaN) on every cell after a
+ * time-out of the in-launch ordering by |gamma| (camp_solver_set_ordering).
+ * All device pointers, written on the handle's stream.
  * CAMP_EINVAL for a non-positive or non-finite tolerance, max_newton < 0 or
  * lin_maxit < 1; CAMP_EUNSUPPORTED beyond 8 rows per lane (n <= 256).
  */

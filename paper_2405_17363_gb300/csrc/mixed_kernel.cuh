@@ -44,7 +44,8 @@ __device__ __forceinline__ void mixed_body(const MixedArgs &a) {
   float *o2 = o1 + a.segV;
   // in-launch difficulty ordering first: it borrows the start of the warp
   // regions (and ends with a block barrier)
-  if (a.ord_ws) order_prologue(a, reinterpret_cast<int *>(smem_raw + sched_smem_bytes(nsch)));
+  if (a.ord_ws)
+    order_prologue<false>(a, reinterpret_cast<int *>(smem_raw + sched_smem_bytes(nsch)));
   for (int i = sl; i < a.segV; i += Lc) {
     g64[i] = 0.0; o64[i] = 0.0; g32[i] = 0.0f; o1[i] = 0.0f; o2[i] = 0.0f;
   }

@@ -573,6 +573,58 @@ camp_status fall_back_to_separate_ordering(camp_solver_t h, Args &a, const doubl
   return separate_ordering(h, a, A_vals, st);
 }
 
+// The in-launch order's entries and class words for `cells` cells ([cells]
+// each), grown on demand; the entries start (and every launch leaves them)
+// all zero.
+camp_status ensure_order_capacity(camp_solver_t h, int cells, cudaStream_t st) {
+  if ((size_t)cells <= h->ord_cap) return CAMP_OK;
+  cudaFree(h->d_ord);
+  h->d_ord = nullptr;
+  h->ord_cap = 0;
+  cudaError_t e;
+  if ((e = cudaMalloc(&h->d_ord, (size_t)cells * 2 * sizeof(int))) != cudaSuccess)
+    return fail(CAMP_ENOMEM, "ordering scratch: %s", cudaGetErrorString(e));
+  if ((e = cudaMemsetAsync(h->d_ord, 0, (size_t)cells * sizeof(int), st)) != cudaSuccess)
+    return cuda_fail(e, "ordering scratch");
+  h->ord_cap = (size_t)cells;
+  return CAMP_OK;
+}
+
+// In-launch ordering of the fused-assembly and Newton launches (orderings 1
+// and 2): cells classified by gamma, as the plain launch classifies them by
+// its sampled diagonal (there is no matrix before a cell is assembled).
+// Leaves a unordered when the warp regions cannot lend the ordering its
+// shared memory.
+camp_status setup_gamma_ordering(camp_solver_t h, WarpArgs &a, size_t smem_free,
+                                 cudaStream_t st) {
+  if (!h->ordering || a.cells <= 1 || smem_free < kOrdSmemBytes) return CAMP_OK;
+  camp_status rs = ensure_order_capacity(h, a.cells, st);
+  if (rs != CAMP_OK) return rs;
+  cudaError_t e;
+  if ((e = ordering_state(h)) != cudaSuccess) return cuda_fail(e, "ordering state");
+  a.ord_out = h->d_ord;
+  a.ord_cls = h->d_ord + h->ord_cap;
+  a.ord_ws = (int *)(h->d_queue + 2 * (1 + kHostSolveStreams));
+  a.ord_err = h->d_ord_err;
+  a.ord_wait = h->ord_wait;
+  a.order = a.ord_out;
+  a.ord_rows = nullptr;
+  a.ord_nrows = 1;
+  a.ord_hits = nullptr;
+  return CAMP_OK;
+}
+
+// A refused cooperative launch of an ordered fused launch runs in index order.
+void drop_gamma_ordering(WarpArgs &a) {
+  (void)cudaGetLastError();
+  a.ord_out = nullptr;
+  a.ord_ws = nullptr;
+  a.ord_cls = nullptr;
+  a.ord_err = nullptr;
+  a.order = nullptr;
+  a.ord_wave = a.ord_stride = 0;
+}
+
 // Difficulty ordering of a warp-packed solve on the handle's own stream (one
 // workspace per handle).  Ordering 1 runs inside the (cooperative) solve
 // launch, borrowing kOrdSmemBytes of the warp regions (smem_free bytes of
@@ -588,16 +640,9 @@ camp_status setup_ordering(camp_solver_t h, Args &a, const double *A_vals, size_
   if (!h->ordering || cells <= 1) return CAMP_OK;
   cudaError_t e = cudaSuccess;
   const bool inl = h->ordering == 1 && smem_free >= kOrdSmemBytes;
-  if (inl && (size_t)cells > h->ord_cap) {
-    cudaFree(h->d_ord);
-    h->d_ord = nullptr;
-    h->ord_cap = 0;
-    if ((e = cudaMalloc(&h->d_ord, (size_t)cells * 2 * sizeof(int))) != cudaSuccess)
-      return fail(CAMP_ENOMEM, "ordering scratch: %s", cudaGetErrorString(e));
-    // the entries start (and are left by every launch) all zero
-    if ((e = cudaMemsetAsync(h->d_ord, 0, (size_t)cells * sizeof(int), st)) != cudaSuccess)
-      return cuda_fail(e, "ordering scratch");
-    h->ord_cap = (size_t)cells;
+  if (inl) {
+    const camp_status rs = ensure_order_capacity(h, cells, st);
+    if (rs != CAMP_OK) return rs;
   }
   if (!inl) return separate_ordering(h, a, A_vals, st);
   if ((e = ordering_state(h)) != cudaSuccess) return cuda_fail(e, "ordering state");
@@ -772,7 +817,7 @@ camp_status do_solve(camp_solver_t h, int cells, const double *A_vals,
 extern "C" {
 
 const char *camp_last_error(void) { return g_err.c_str(); }
-const char *camp_version(void) { return "campsolve 0.14 (sm_103a)"; }
+const char *camp_version(void) { return "campsolve 0.15 (sm_103a)"; }
 
 camp_status camp_schedule_build(int n, int nnz, const int *row_ptr,
                                 const int *col_idx, int lanes_per_cell,
@@ -1331,8 +1376,16 @@ camp_status camp_solver_assemble_solve(camp_solver_t h, int cells,
   if ((e = assemble_occupancy(E, wpb, smem, &occ)) != cudaSuccess) return cuda_fail(e, "occupancy");
   if (occ < 1) occ = 1;
   const int grid = std::max(1, std::min((a.ngroups + wpb - 1) / wpb, h->sms * occ));
-  if ((e = launch_assemble(E, a, wpb, grid, smem, h->stream)) != cudaSuccess)
-    return cuda_fail(e, "assembly kernel launch");
+  rc = setup_gamma_ordering(h, a, smem - sched_smem_bytes(a.L * a.Lc), h->stream);
+  if (rc != CAMP_OK) return rc;
+  set_wave(a, grid, wpb);
+  e = launch_cooperative(h, a.ord_ws != nullptr,
+                         [&] { return launch_assemble(E, a, wpb, grid, smem, h->stream); });
+  if (e == cudaErrorCooperativeLaunchTooLarge && a.ord_ws) {
+    drop_gamma_ordering(a);
+    e = launch_assemble(E, a, wpb, grid, smem, h->stream);
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "assembly kernel launch");
   return CAMP_OK;
 }
 
@@ -1370,8 +1423,16 @@ camp_status camp_solver_newton_solve(camp_solver_t h, int cells,
   if ((e = newton_occupancy(E, wpb, smem, &occ)) != cudaSuccess) return cuda_fail(e, "occupancy");
   if (occ < 1) occ = 1;
   const int grid = std::max(1, std::min((a.ngroups + wpb - 1) / wpb, h->sms * occ));
-  if ((e = launch_newton(E, a, wpb, grid, smem, h->stream)) != cudaSuccess)
-    return cuda_fail(e, "Newton kernel launch");
+  rc = setup_gamma_ordering(h, a, smem - sched_smem_bytes(a.L * a.Lc), h->stream);
+  if (rc != CAMP_OK) return rc;
+  set_wave(a, grid, wpb);
+  e = launch_cooperative(h, a.ord_ws != nullptr,
+                         [&] { return launch_newton(E, a, wpb, grid, smem, h->stream); });
+  if (e == cudaErrorCooperativeLaunchTooLarge && a.ord_ws) {
+    drop_gamma_ordering(a);
+    e = launch_newton(E, a, wpb, grid, smem, h->stream);
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "Newton kernel launch");
   return CAMP_OK;
 }
 

@@ -23,6 +23,10 @@ __device__ __forceinline__ int difficulty_class(unsigned hi) {
 __device__ __forceinline__ unsigned diag_departure_hi(double aii) {
   return (unsigned)((unsigned long long)__double_as_longlong(fabs(aii - 1.0)) >> 32);
 }
+// The same key from gamma itself (its magnitude, on the integer pipe).
+__device__ __forceinline__ unsigned magnitude_hi(double v) {
+  return (unsigned)(((unsigned long long)__double_as_longlong(v) & 0x7fffffffffffffffull) >> 32);
+}
 
 __device__ __forceinline__ bool is_finite_bits(double v) {
   const unsigned long long u = (unsigned long long)__double_as_longlong(v);
@@ -470,8 +474,8 @@ __device__ __forceinline__ void grid_barrier_bounded(unsigned *ctr, unsigned tar
 // In-launch difficulty ordering (run by every CTA of a cooperative solve
 // launch before it solves; Args: WarpArgs or MixedArgs).  The estimate, the classes and the hardest-first
 // order are those of the separate ordering pass: max_i |A_ii - 1| binned on
-// half octaves, here over the sampled diagonal rows.  Each CTA classifies a
-// contiguous share of the cells, counts them per class in shared memory and
+// half octaves, here over the sampled diagonal rows (or of |gamma_c|, see
+// BY_GAMMA).  Each CTA classifies a contiguous share of the cells, counts them per class in shared memory and
 // reserves its range inside each class with one global atomic per class;
 // after a grid barrier it turns the class totals into class starts and
 // writes its cells' order entries (cell + 1).  A warp that takes a group
@@ -479,7 +483,13 @@ __device__ __forceinline__ void grid_barrier_bounded(unsigned *ctr, unsigned tar
 // all resident and past the barrier) and clears them once it has read them,
 // so the order is all zero again for the next launch.
 // sm: kOrdSmemBytes of this CTA's shared memory not yet in use.
-template <class Args>
+// BY_GAMMA: classify by |gamma_c| instead (the fused assembly and Newton
+// launches, whose matrices do not exist before a cell is assembled; gamma
+// scales the off-identity part of A = I - gamma J, so it ranks the cells as
+// the diagonal estimate does).
+__device__ __forceinline__ const double *ord_gamma_of(const WarpArgs &a) { return a.gamma; }
+__device__ __forceinline__ const double *ord_gamma_of(const MixedArgs &) { return nullptr; }
+template <bool BY_GAMMA, class Args>
 __device__ __forceinline__ void order_prologue(const Args &a, int *sm) {
   int *hist = sm;                       // per class: count, then class start
   int *base = sm + kOrdClasses;         // per class: this CTA's offset inside it
@@ -490,7 +500,7 @@ __device__ __forceinline__ void order_prologue(const Args &a, int *sm) {
   unsigned *ctr = reinterpret_cast<unsigned *>(a.ord_ws + kOrdClasses);
   const int per = (a.cells + gridDim.x - 1) / gridDim.x;
   const int c0 = min(a.cells, (int)blockIdx.x * per), c1 = min(a.cells, c0 + per);
-  const int nr = a.ord_nrows;
+  const int nr = BY_GAMMA ? 1 : a.ord_nrows;
   // a share of one pass keeps its class words in shared memory
   const bool one_piece = c1 - c0 <= kOrdPiece;
   for (int i = threadIdx.x; i < kOrdClasses; i += blockDim.x) hist[i] = 0;
@@ -511,12 +521,16 @@ __device__ __forceinline__ void order_prologue(const Args &a, int *sm) {
         cl[u] = j < m ? j / nr : -1;
         q[u] = j - cl[u] * nr;
         if (cl[u] >= 0)
-          v[u] = __ldg(a.A + (size_t)(p0 + cl[u]) * a.nnz + __ldg(a.ord_rows + q[u]));
+          v[u] = BY_GAMMA ? __ldg(ord_gamma_of(a) + p0 + cl[u])
+                          : __ldg(a.A + (size_t)(p0 + cl[u]) * a.nnz + __ldg(a.ord_rows + q[u]));
       }
 #pragma unroll
       for (int u = 0; u < kOrdBatch; ++u)
         if (cl[u] >= 0)
-          atomicMax(key + cl[u], (unsigned long long)diag_departure_hi(v[u]) << 32 | (unsigned)q[u]);
+          atomicMax(key + cl[u], (unsigned long long)(BY_GAMMA ? magnitude_hi(v[u])
+                                                               : diag_departure_hi(v[u]))
+                                         << 32 |
+                                     (unsigned)q[u]);
     }
     __syncthreads();
     for (int i = threadIdx.x; i < pc; i += blockDim.x) {

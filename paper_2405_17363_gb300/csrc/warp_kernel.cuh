@@ -530,9 +530,8 @@ __device__ __forceinline__ void plain_launch_body(const WarpArgs &a) {
                   (size_t)warp * a.k * a.segStride;
   const SchedWord *sch = sch_s + (lane & (a.Lc - 1));
   const int warps_total = gridDim.x * (blockDim.x >> 5);
-  if constexpr (SRC == kSrcStaged) {
-    if (a.ord_ws) order_prologue(a, reinterpret_cast<int *>(smem_raw + sched_smem_bytes(nsch)));
-  }
+  if (a.ord_ws)
+    order_prologue<SRC != kSrcStaged>(a, reinterpret_cast<int *>(smem_raw + sched_smem_bytes(nsch)));
   auto run = [&](auto lc) {
     constexpr int LC = decltype(lc)::value;
     if (!a.queue) {
@@ -564,8 +563,7 @@ __device__ __forceinline__ void plain_launch_body(const WarpArgs &a) {
       // in-launch ordering: wait for this group's order entries, solve,
       // then clear them
       const int p = (int)g * (LC ? 32 / LC : a.k) + lane;
-      const bool mine =
-          SRC == kSrcStaged && a.ord_ws && lane < (LC ? 32 / LC : a.k) && p < a.cells;
+      const bool mine = a.ord_ws && lane < (LC ? 32 / LC : a.k) && p < a.cells;
       if (mine) wait_order_entry(a.order + p, a.ord_ws + kOrdFlag, a.ord_err, a.ord_wait);
       __syncwarp();
       solve_group<E, SRC, LC>(a, (int)g, wbase, sch);
@@ -586,7 +584,7 @@ __device__ __forceinline__ void plain_launch_body(const WarpArgs &a) {
   if (!a.queue) return;
   // the last warp resets the queue and the ordering workspace (and, after a
   // time-out of the ordering, marks the launch's cells invalid)
-  finish_queue(a, SRC == kSrcStaged, warps_total, lane);
+  finish_queue(a, true, warps_total, lane);
 }
 
 template <int E>

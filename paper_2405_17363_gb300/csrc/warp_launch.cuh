@@ -11,6 +11,11 @@
                                   size_t smem, cudaStream_t st) {               \
     cudaError_t e = ensure_max_smem((const void *)kernel<E>);                   \
     if (e != cudaSuccess) return e;                                             \
+    if (a.ord_ws) { /* in-launch ordering: every CTA resident */                \
+      void *args[] = {(void *)&a};                                              \
+      return cudaLaunchCooperativeKernel((const void *)kernel<E>, dim3(grid),   \
+                                         dim3(wpb * 32), args, smem, st);       \
+    }                                                                           \
     kernel<E><<<grid, wpb * 32, smem, st>>>(a);                                 \
     return cudaGetLastError();                                                  \
   }                                                                             \

@@ -151,3 +151,33 @@ def test_newton_argument_errors(cuda):
             s.newton_solve(a, g, a, **kw)
         assert ex.value.code == camp.CAMP_EINVAL
     s.close()
+
+
+def test_newton_ordering_is_bitwise_neutral(cuda):
+    """The Newton launch orders its cells hardest first by gamma inside the
+    launch: bitwise the index-order results (orderings 1 and 2, and a refused
+    cooperative launch, which runs in index order)."""
+    import torch
+    from paper_2405_17363_gb300 import camp
+    cbs, _, _ = synth.workload(1, cells=3001)
+    cb = cbs[0]
+    m = cb.mech
+    s = camp.Solver(m.row_ptr, m.col_idx)
+    s.set_mechanism(*_mech_args(m))
+    a = torch.as_tensor(cb.conc, device=cuda)
+    g = torch.as_tensor(cb.gamma, device=cuda)
+
+    def run():
+        out = s.newton_solve(a, g, a.clone(), newton_tol=NEWTON_TOL)
+        torch.cuda.synchronize()
+        return {k: v.clone() for k, v in out.items()}
+    s.set_ordering(0)
+    ref = run()
+    for mode, hooks in ((1, {}), (2, {}), (1, {"refuse_cooperative": True})):
+        s.set_ordering(mode)
+        s.set_test_hooks(**hooks)
+        got = run()
+        for k in ref:
+            assert torch.equal(ref[k], got[k]), (k, mode, hooks)
+        s.set_test_hooks()
+    s.close()
