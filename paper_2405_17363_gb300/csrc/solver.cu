@@ -836,8 +836,11 @@ camp_status camp_schedule_build(int n, int nnz, const int *row_ptr,
       return fail(CAMP_EPATTERN, "row_ptr not nondecreasing within [0, nnz] at row %d", i);
   std::vector<int> rp(row_ptr, row_ptr + n + 1), ci(col_idx, col_idx + nnz), diag(n, -1);
   for (int i = 0; i < n; ++i) {
-    for (int k = rp[i]; k < rp[i + 1]; ++k)
+    for (int k = rp[i]; k < rp[i + 1]; ++k) {
+      if (ci[k] < 0 || ci[k] >= n)
+        return fail(CAMP_EPATTERN, "column %d out of range at entry %d", ci[k], k);
       if (ci[k] == i) diag[i] = k;
+    }
     if (diag[i] < 0) return fail(CAMP_EPATTERN, "diagonal entry missing in row %d", i);
   }
   Schedule S = build_schedule(n, rp, ci, std::vector<int>(), diag, lanes_per_cell);

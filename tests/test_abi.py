@@ -251,3 +251,22 @@ def test_committed_traffic_figure_matches_the_library_revision(lib):
     traffic = bench.measured_traffic(version)
     assert traffic is not None and 40e6 < traffic < 80e6, (version, traffic)
     assert bench.measured_traffic("campsolve 0.0 (none)") is None
+
+
+def test_schedule_build_rejects_columns_out_of_range(lib):
+    """camp_schedule_build checks every column index against [0, n) before
+    the schedule builder uses it (a negative or too large column would index
+    its residue tables out of range)."""
+    EPATTERN = -4
+    f = lib.camp_schedule_build
+    f.restype = ctypes.c_int
+    f.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
+                  ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]
+    rp = np.array([0, 2, 4, 5], np.int32)
+    L = ctypes.c_int()
+    for bad in (-1, 3, 4000):
+        ci = np.array([0, bad, 0, 1, 2], np.int32)
+        assert f(3, 5, rp.ctypes.data, ci.ctypes.data, 1, None, 0, ctypes.byref(L)) == EPATTERN
+        assert "out of range" in _msg(lib)
+    ci = np.array([0, 2, 0, 1, 2], np.int32)
+    assert f(3, 5, rp.ctypes.data, ci.ctypes.data, 1, None, 0, ctypes.byref(L)) == 0
