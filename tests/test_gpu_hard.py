@@ -205,3 +205,36 @@ def test_hard_regime_mixed_refinement(camp, cuda, hard):
     print(f"hard mixed: statuses gpu {np.bincount(gpu['status'], minlength=4).tolist()} oracle "
           f"{np.bincount(orc['status'], minlength=4).tolist()}; error vs FP64 oracle max "
           f"{err[conv].max():.2e} p99 {np.percentile(err[conv], 99):.2e}; {res}")
+
+
+def test_hard_regime_fused_assembly_all_cells(camp, cuda, hard):
+    """The fused assembly + solve (A = I - gamma J(conc) built in shared
+    memory, cells ordered by gamma inside the launch) on the hard cells,
+    every cell against the oracle's plain-C assembly followed by the oracle
+    solve, with the rounding-sensitive bar; and the gamma ordering leaves the
+    results bitwise those of index order on these long, uneven solves."""
+    import torch
+    cb = hard
+    m = cb.mech
+    tol, maxit = 1e-10, 500
+    s = camp.Solver(m.row_ptr, m.col_idx)
+    s.set_mechanism(m.reactants[:, 0], m.reactants[:, 1], m.products, m.k)
+    conc = torch.as_tensor(cb.conc, device=cuda)
+    gam = torch.as_tensor(cb.gamma, device=cuda)
+    b = torch.as_tensor(cb.b, device=cuda)
+    got = [t.clone() for t in s.assemble_solve(conc, gam, b, tol, maxit)]
+    s.set_ordering(0)
+    ref = s.assemble_solve(conc, gam, b, tol, maxit)
+    torch.cuda.synchronize()
+    for r, g in zip(ref, got):
+        assert torch.equal(r, g)
+    s.close()
+    gpu = dict(x=got[0].cpu().numpy(), iters=got[1].cpu().numpy(), resid=got[2].cpu().numpy(),
+               status=got[3].cpu().numpy())
+    A = oracle.assemble(m.row_ptr, m.col_idx, m.reactants[:, 0], m.reactants[:, 1], m.products,
+                        m.k, cb.conc, cb.gamma)
+    orc, pert = _oracles(m, A, cb.b, tol, maxit)
+    assert orc["iters"].mean() >= 30
+    res = parity.compare_sensitive(m, A, cb.b, tol, maxit, gpu, orc, pert, "hard fused")
+    print(f"hard fused: oracle mean iters {orc['iters'].mean():.2f}, gpu "
+          f"{gpu['iters'].mean():.2f}; {res}")
