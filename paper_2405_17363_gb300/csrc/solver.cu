@@ -1106,29 +1106,13 @@ camp_status camp_solver_solve_host(camp_solver_t h, int cells,
   if (!h->h_start && (e = cudaEventCreateWithFlags(&h->h_start, cudaEventDisableTiming)) != cudaSuccess)
     return cuda_fail(e, "event create");
   cudaEventRecord(h->h_start, h->stream);
-  for (int q = 0; q < 2 + kHostSolveStreams; ++q) cudaStreamWaitEvent(h->h_streams[q], h->h_start, 0);
-  // Outputs in host memory the device can address (pinned or mapped) are
-  // written by the kernels directly; otherwise they are staged on the device
-  // and copied back per chunk.
-  auto device_view = [](const void *p) -> void * {
-    cudaPointerAttributes pa;
-    if (cudaPointerGetAttributes(&pa, p) != cudaSuccess) {
-      cudaGetLastError();
-      return nullptr;
-    }
-    return (pa.type == cudaMemoryTypeHost || pa.type == cudaMemoryTypeManaged) ? pa.devicePointer
-                                                                               : nullptr;
-  };
-  double *dx = (double *)device_view(x);
-  int *dit = (int *)device_view(iters_out);
-  double *dres = (double *)device_view(resid_out);
-  int *dst = status_out ? (int *)device_view(status_out) : nullptr;
-  const bool direct = dx && dit && dres && (!status_out || dst);
+  cudaStreamWaitEvent(sin, h->h_start, 0);
   // Pipeline: b in one copy, then A in chunks of shrinking size back to back
   // on the copy-in stream (few large copies keep the host link busy; a small
   // last chunk keeps the solve after the last byte short); each chunk's solve
   // starts on the next solve stream once its A has landed, so the solves of
-  // consecutive chunks overlap.
+  // consecutive chunks overlap.  The copies are enqueued first: the link
+  // starts while the host sets up the rest.
   int nchunk = 1;
   while (nchunk < kHostChunks && cells >= (nchunk + 1) * 1024) ++nchunk;
   int c0s[kHostChunks + 1];
@@ -1149,6 +1133,24 @@ camp_status camp_solver_solve_host(camp_solver_t h, int cells,
                     (size_t)cn * nnz * 8, cudaMemcpyHostToDevice, sin);
     cudaEventRecord(h->h_in[q], sin);
   }
+  for (int q = 1; q < 2 + kHostSolveStreams; ++q) cudaStreamWaitEvent(h->h_streams[q], h->h_start, 0);
+  // Outputs in host memory the device can address (pinned or mapped) are
+  // written by the kernels directly; otherwise they are staged on the device
+  // and copied back per chunk.
+  auto device_view = [](const void *p) -> void * {
+    cudaPointerAttributes pa;
+    if (cudaPointerGetAttributes(&pa, p) != cudaSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
+    return (pa.type == cudaMemoryTypeHost || pa.type == cudaMemoryTypeManaged) ? pa.devicePointer
+                                                                               : nullptr;
+  };
+  double *dx = (double *)device_view(x);
+  int *dit = (int *)device_view(iters_out);
+  double *dres = (double *)device_view(resid_out);
+  int *dst = status_out ? (int *)device_view(status_out) : nullptr;
+  const bool direct = dx && dit && dres && (!status_out || dst);
   camp_status rs = CAMP_OK;
   for (int q = 0; q < nchunk; ++q) {
     const int c0 = c0s[q], cn = c0s[q + 1] - c0;
