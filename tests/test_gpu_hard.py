@@ -238,3 +238,27 @@ def test_hard_regime_fused_assembly_all_cells(camp, cuda, hard):
     res = parity.compare_sensitive(m, A, cb.b, tol, maxit, gpu, orc, pert, "hard fused")
     print(f"hard fused: oracle mean iters {orc['iters'].mean():.2f}, gpu "
           f"{gpu['iters'].mean():.2f}; {res}")
+
+
+def test_hard_regime_every_arrangement(camp, cuda, hard):
+    """Every warp-packed lane count and every Block-cells(k) arrangement (per-
+    cell scalars) on the hard cells at 1e-10 / 500, every cell against the
+    oracle with the rounding-sensitive bar: the paths the easy workloads
+    rarely reach (long iterations, residual-replacement restarts, the
+    iteration cap of the slowest cells) under every lane count, rows per lane
+    and block layout."""
+    from tests.test_gpu_solve import arrangements, run_gpu
+    cb = hard
+    m = cb.mech
+    tol, maxit = 1e-10, 500
+    orc, pert = _oracles(m, cb.A_vals, cb.b, tol, maxit)
+    names = []
+    for name, arr in arrangements(m.n):
+        if arr is None:
+            continue  # the automatic arrangement: test_hard_regime_all_cells
+        gpu = run_gpu(camp, m, cb.A_vals, cb.b, tol, maxit, cuda, arr)
+        res = parity.compare_sensitive(m, cb.A_vals, cb.b, tol, maxit, gpu, orc, pert,
+                                       f"hard/{name}")
+        names.append(name)
+        print(f"hard/{name}: gpu mean iters {gpu['iters'].mean():.2f}; {res['gpu']}")
+    assert {"warp8", "warp16", "warp32", "block1", "block2", "block3"} <= set(names)
