@@ -90,8 +90,10 @@ def compare_sensitive(mech, A_vals, b, tol, maxit, gpu, orc, orc_perturbed, labe
                       max_fallback=0):
     """Parity on systems whose iteration is sensitive to rounding.
 
-    orc: the oracle on (A_vals, b); orc_perturbed: the oracle on right-hand
-    sides one rounding away (``perturbed_rhs``), a list of at least one.
+    orc: the oracle on (A_vals, b); orc_perturbed: the oracle on inputs one
+    rounding away (``perturbed_rhs``: the right-hand sides, and an initial
+    guess where one is given, since r0 = b - A x0 then rounds at the scale of
+    A x0), a list of at least one.
 
     Per cell, every cell: a converged status means a true residual <= tol, a
     MAXIT status means maxit iterations and a residual above tol; where both

@@ -262,3 +262,49 @@ def test_hard_regime_every_arrangement(camp, cuda, hard):
         names.append(name)
         print(f"hard/{name}: gpu mean iters {gpu['iters'].mean():.2f}; {res['gpu']}")
     assert {"warp8", "warp16", "warp32", "block1", "block2", "block3"} <= set(names)
+
+
+def test_hard_regime_initial_guess_and_host_entry(camp, cuda, hard):
+    """On the hard cells: a given initial guess (CAMP_X0_GIVEN: r = b - A x0
+    first) against the oracle started from the same guess, with the
+    rounding-sensitive bar (the oracle's own spread measured with b and the
+    guess one rounding away); and the host-memory entry point (chunked copies,
+    chunk solves in index order on other streams) bitwise equal to the device
+    solve."""
+    import torch
+    cb = hard
+    m = cb.mech
+    tol, maxit = 1e-10, 500
+    x0 = np.random.default_rng(11).standard_normal((cb.cells, m.n))
+    s = camp.Solver(m.row_ptr, m.col_idx)
+    A = torch.as_tensor(cb.A_vals, device=cuda)
+    b = torch.as_tensor(cb.b, device=cuda)
+    x, it, res, st = s.solve(A, b, tol, maxit, x0=torch.as_tensor(x0, device=cuda))
+    torch.cuda.synchronize()
+    gpu = dict(x=x.cpu().numpy(), iters=it.cpu().numpy(), resid=res.cpu().numpy(),
+               status=st.cpu().numpy())
+    orc = oracle.solve(m.row_ptr, m.col_idx, cb.A_vals, cb.b, tol, maxit, x0=x0,
+                       threads=THREADS)
+    # the inputs one rounding away: b and the guess (r0 = b - A x0 is dominated by A x0 here,
+    # so a change of b alone moves it far less than the rounding of A x0 does)
+    pert = [oracle.solve(m.row_ptr, m.col_idx, cb.A_vals, parity.perturbed_rhs(cb.b, seed), tol,
+                         maxit, x0=parity.perturbed_rhs(x0, seed + 10), threads=THREADS)
+            for seed in (1, 2)]
+    assert orc["iters"].mean() >= 30
+    res_x0 = parity.compare_sensitive(m, cb.A_vals, cb.b, tol, maxit, gpu, orc, pert, "hard x0")
+    xd, itd, rd, sd = s.solve(A, b, tol, maxit)
+    torch.cuda.synchronize()
+    C = cb.cells
+    hA = torch.as_tensor(cb.A_vals).pin_memory()
+    hb = torch.as_tensor(cb.b).pin_memory()
+    hx = torch.full((C, m.n), np.nan, dtype=torch.float64).pin_memory()
+    hit = torch.full((C,), -7, dtype=torch.int32).pin_memory()
+    hr = torch.full((C,), np.nan, dtype=torch.float64).pin_memory()
+    hs = torch.full((C,), -7, dtype=torch.int32).pin_memory()
+    camp.camp_solver_solve_host(s.h, C, hA, hb, hx, tol, maxit, hit, hr, hs)
+    np.testing.assert_array_equal(hx.numpy(), xd.cpu().numpy())
+    np.testing.assert_array_equal(hit.numpy(), itd.cpu().numpy())
+    np.testing.assert_array_equal(hr.numpy(), rd.cpu().numpy())
+    np.testing.assert_array_equal(hs.numpy(), sd.cpu().numpy())
+    s.close()
+    print(f"hard x0: {res_x0['gpu']}")

@@ -127,3 +127,28 @@ def test_noalloc_rejects_a_pattern_larger_than_its_scratch(cuda):
     code, _ = _noalloc(lib, mech, A, b, 1e-10, 10, torch, cuda)
     assert code == camp.CAMP_EUNSUPPORTED
     assert "static scratch" in camp.camp_last_error()
+
+
+def test_noalloc_hard_regime_bitwise_handle(cuda):
+    """The hard cells (tens to hundreds of iterations per cell, residual
+    replacement on some): the allocation-free call gives bitwise the handle's
+    index-order results, whose parity with the oracle the hard-regime tests
+    check."""
+    import torch
+    from paper_2405_17363_gb300 import camp
+    lib = camp._lib
+    cbs, tol, maxit = synth.workload(5)
+    cb = cbs[0]
+    m = cb.mech
+    A = torch.as_tensor(cb.A_vals, device=cuda)
+    b = torch.as_tensor(cb.b, device=cuda)
+    code, out = _noalloc(lib, m, A, b, tol, maxit, torch, cuda)
+    assert code == camp.CAMP_OK, camp.camp_last_error()
+    s = camp.Solver(m.row_ptr, m.col_idx)
+    s.set_ordering(0)
+    ref = s.solve(A, b, tol, maxit)
+    torch.cuda.synchronize()
+    assert float(ref[1].double().mean().item()) >= 30
+    for g, r in zip(out, ref):
+        assert torch.equal(g, r)
+    s.close()
