@@ -71,3 +71,40 @@ def test_coupling_costs_iterations_only_on_varied_cells(cuda):
     for cpb in (2, 3, 12):
         g = _run(camp, m, A, b, tol, maxit, cpb, cuda)
         assert np.all(np.abs(g["iters"] - one["iters"][0]) <= 1)
+
+
+@pytest.mark.parametrize("cpb", [2, 3, 12])
+def test_coupled_hard_regime_against_block_diagonal_oracle(cuda, cpb):
+    """Coupled Block-cells(k) on the hard cells (600 of them, blocks of k):
+    every block against the oracle on its block-diagonal system, with the
+    rounding-sensitive bar (the blocks' systems iterate tens to hundreds of
+    times, where rounding moves counts); all cells of a block report the
+    block's count, residual and status."""
+    import os
+    from paper_2405_17363_gb300 import camp
+    cbs, tol, maxit = synth.workload(5)
+    cb = cbs[0]
+    m = cb.mech
+    C = 600
+    A, b = cb.A_vals[:C], cb.b[:C]
+    gpu = _run(camp, m, A, b, tol, maxit, cpb, cuda)
+    nb = C // cpb
+    for key in ("iters", "resid", "status"):
+        per = gpu[key].reshape(nb, cpb)
+        assert np.all(per == per[:, :1]), key
+    rp, ci, _, _ = parity.block_diagonal(m, A, b, 0, cpb)
+    mblk = synth.Mechanism(n=cpb * m.n, R=0, reactants=None, products=None, k=None,
+                           row_ptr=rp, col_idx=ci)
+    Ab = np.ascontiguousarray(A.reshape(nb, cpb * m.nnz))
+    bb = np.ascontiguousarray(b.reshape(nb, cpb * m.n))
+    gblk = dict(x=gpu["x"].reshape(nb, cpb * m.n), iters=gpu["iters"][::cpb],
+                resid=gpu["resid"][::cpb], status=gpu["status"][::cpb])
+    threads = os.cpu_count() or 8
+    orc = oracle.solve(rp, ci, Ab, bb, tol, maxit, threads=threads)
+    pert = [oracle.solve(rp, ci, Ab, parity.perturbed_rhs(bb, seed), tol, maxit, threads=threads)
+            for seed in (1, 2)]
+    assert orc["iters"].mean() >= 30
+    res = parity.compare_sensitive(mblk, Ab, bb, tol, maxit, gblk, orc, pert,
+                                   f"coupled hard k={cpb}")
+    print(f"coupled hard k={cpb}: oracle mean iters {orc['iters'].mean():.1f}, gpu "
+          f"{gblk['iters'].mean():.1f}; {res['gpu']} vs oracle {res['oracle_perturbed']}")
