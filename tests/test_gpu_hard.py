@@ -240,17 +240,17 @@ def test_hard_regime_fused_assembly_all_cells(camp, cuda, hard):
           f"{gpu['iters'].mean():.2f}; {res}")
 
 
-def test_hard_regime_every_arrangement(camp, cuda, hard):
+@pytest.mark.parametrize("tol,maxit", [(1e-10, 500), (1e-10, 30), (1e-15, 500)])
+def test_hard_regime_every_arrangement(camp, cuda, hard, tol, maxit):
     """Every warp-packed lane count and every Block-cells(k) arrangement (per-
-    cell scalars) on the hard cells at 1e-10 / 500, every cell against the
-    oracle with the rounding-sensitive bar: the paths the easy workloads
-    rarely reach (long iterations, residual-replacement restarts, the
-    iteration cap of the slowest cells) under every lane count, rows per lane
-    and block layout."""
+    cell scalars) on the hard cells, every cell against the oracle with the
+    rounding-sensitive bar, in the three cases of test_hard_regime_all_cells
+    (long iterations, the iteration cap for most cells, residual-replacement
+    restarts at tol 1e-15): the paths the easy workloads rarely reach, under
+    every lane count, rows per lane and block layout."""
     from tests.test_gpu_solve import arrangements, run_gpu
     cb = hard
     m = cb.mech
-    tol, maxit = 1e-10, 500
     orc, pert = _oracles(m, cb.A_vals, cb.b, tol, maxit)
     names = []
     for name, arr in arrangements(m.n):
@@ -258,9 +258,10 @@ def test_hard_regime_every_arrangement(camp, cuda, hard):
             continue  # the automatic arrangement: test_hard_regime_all_cells
         gpu = run_gpu(camp, m, cb.A_vals, cb.b, tol, maxit, cuda, arr)
         res = parity.compare_sensitive(m, cb.A_vals, cb.b, tol, maxit, gpu, orc, pert,
-                                       f"hard/{name}")
+                                       f"hard/{name} tol {tol} maxit {maxit}")
         names.append(name)
-        print(f"hard/{name}: gpu mean iters {gpu['iters'].mean():.2f}; {res['gpu']}")
+        print(f"hard/{name} tol {tol} maxit {maxit}: gpu mean iters {gpu['iters'].mean():.2f}; "
+              f"{res['gpu']}")
     assert {"warp8", "warp16", "warp32", "block1", "block2", "block3"} <= set(names)
 
 
