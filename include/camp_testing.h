@@ -28,6 +28,34 @@ extern "C" {
 camp_status camp_solver_set_test_hooks(camp_solver_t h, long long ordering_wait_cycles,
                                        int refuse_cooperative);
 
+/*
+ * Single-cell tickets of the plain warp-packed solve at 16 lanes per cell:
+ * the launch may solve some cells one per warp on all 32 lanes (the end of a
+ * large batch, where a lone warp's latency decides the launch's length, and
+ * small batches), on a split schedule that keeps every operation of the pair
+ * solve, so the results are bit for bit those of the pair solve.  pairs < 0:
+ * the library's automatic choice (the default); 0: none; k > 0: the last k
+ * pair tickets of every such launch become 2k single-cell tickets (at most
+ * all of them).  Host setting only; nothing is enqueued.  CAMP_EINVAL for a
+ * null handle.
+ */
+camp_status camp_solver_set_single_tail(camp_solver_t h, int pairs);
+
+/*
+ * The split schedule behind single-cell tickets (host only, no GPU), for a
+ * pattern as camp_solver_create takes it: one cell on 32 lanes, lane v and
+ * lane v + 16 taking the rows of lane v of the 16-lane schedule
+ * (camp_schedule_build with lanes_per_cell 16), divided at a row boundary,
+ * every row's slots in the same order.  Layout and arguments as
+ * camp_schedule_build, with 32 lanes: words (may be NULL to query
+ * slots_per_lane) receives slots_per_lane * 32 slots [slot][lane], two uint32
+ * per slot (entry or 0xFFFFFFFF, then the slot word).  CAMP_EUNSUPPORTED
+ * when the pattern's 16-lane schedule would use more than 5 rows per lane.
+ */
+camp_status camp_schedule_build_split(int n, int nnz, const int *row_ptr,
+                                      const int *col_idx, unsigned *words,
+                                      int capacity_slots, int *slots_per_lane);
+
 #ifdef __cplusplus
 }
 #endif

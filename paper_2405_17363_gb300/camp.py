@@ -49,6 +49,7 @@ _set_arr = _sig("camp_solver_set_arrangement", [_P, _I, _I, _I, _I])
 _set_ordering = _sig("camp_solver_set_ordering", [_P, _I])
 _get_fault = _sig("camp_solver_get_fault", [_P, ctypes.POINTER(_I)])
 _set_test_hooks = _sig("camp_solver_set_test_hooks", [_P, ctypes.c_longlong, _I])
+_set_single_tail = _sig("camp_solver_set_single_tail", [_P, _I])
 _solve = _sig("camp_solver_solve", [_P, _I, _P, _P, _P, _D, _I, _P, _P])
 _solve_ex = _sig("camp_solver_solve_ex", [_P, _I, _P, _P, _P, _D, _I, _P, _P, _P, _I])
 _grad_A = _sig("camp_solver_grad_A", [_P, _I, _P, _P, _P])
@@ -156,6 +157,12 @@ def camp_solver_get_fault(h: int) -> bool:
     v = _I(0)
     _check(_get_fault(h, ctypes.byref(v)), "camp_solver_get_fault")
     return bool(v.value)
+
+
+def camp_solver_set_single_tail(h: int, pairs: int) -> None:
+    """Single-cell tickets of the plain 16-lane launch (include/camp_testing.h):
+    pairs < 0 automatic, 0 none, k > 0 the last k pairs as single cells."""
+    _check(_set_single_tail(h, int(pairs)), "camp_solver_set_single_tail")
 
 
 def camp_solver_set_test_hooks(h: int, ordering_wait_cycles: int = 0,
@@ -332,6 +339,9 @@ class Solver:
 
     def set_test_hooks(self, ordering_wait_cycles: int = 0, refuse_cooperative: bool = False):
         camp_solver_set_test_hooks(self.h, ordering_wait_cycles, refuse_cooperative)
+
+    def set_single_tail(self, pairs: int):
+        camp_solver_set_single_tail(self.h, pairs)
 
     def solve(self, A_vals, b, tol=1e-10, maxit=500, x0=None, transpose=False,
               out=None):

@@ -43,6 +43,19 @@ struct WarpArgs {
   const int *dst;          // [nnz] slot of each A entry (pattern order): inverse of src
   const int *padfrom;      // [Lc] first padding slot of each lane
   const int *dslot;        // [n] slot of each row's diagonal entry
+  // Single-cell tickets (the plain launch at 16 lanes per cell): tickets t <
+  // single_from solve the pair at positions 2t, 2t+1; tickets t >= single_from
+  // solve the one cell at position 2 * single_from + (t - single_from) with
+  // all 32 lanes, bit for bit as its pair would (split schedule below: each
+  // 16-lane lane's rows divided between lanes v and v + 16, every row's
+  // entries in the same order).  No single tickets when sched2 is null or
+  // single_from >= ngroups.
+  int single_from;
+  int L2;                  // slots per lane of the split schedule
+  const SchedWord *sched2; // [L2 x 32]
+  const int *dst2;         // [nnz] split slot of each A entry
+  const int *padfrom2;     // [32] first padding slot of each lane
+  const int *dslot2;       // [n] split slot of each row's diagonal entry
   double tol;
   int maxit;
   int x0_given;

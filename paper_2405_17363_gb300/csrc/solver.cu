@@ -207,7 +207,94 @@ struct Schedule {
   int auto_wpb[3] = {0, 0, 0};
   SchedWord *d_words = nullptr;
   int *d_src = nullptr, *d_dslot = nullptr, *d_dst = nullptr, *d_padfrom = nullptr;
+  // 16 lanes per cell only: the split schedule of one cell on 32 lanes (L2
+  // 0: none); see split_schedule
+  int L2 = 0;
+  std::vector<SchedWord> words2;  // [L2][32]
+  std::vector<int> dst2, padfrom2, dslot2;
+  SchedWord *d_words2 = nullptr;
+  int *d_dst2 = nullptr, *d_padfrom2 = nullptr, *d_dslot2 = nullptr;
 };
+
+// The split schedule of a 16-lane schedule: one cell on all 32 lanes, lane v
+// and lane v + 16 sharing the rows of 16-lane lane v, whole rows to either
+// side (the subset that balances the two sides' slot counts best, found
+// exhaustively for up to 16 rows, else greedily longest first); every row
+// keeps its slots' order, so each row's sum is the same chain of
+// multiply-adds as in the pair solve; padding slots multiply zero by column
+// 0.  Fills L2, words2, dst2, padfrom2 and dslot2 (L2 stays 0 unless the
+// schedule is 16 lanes wide).
+void split_schedule(Schedule &S, int n, int nnz) {
+  if (S.Lc != 16 || S.L == 0) return;
+  std::vector<std::vector<int>> rstart(16), rlen(16);
+  std::vector<unsigned> side(16, 0u);  // bit r: row r of the lane goes to lane v + 16
+  int L2 = 1;
+  for (int v = 0; v < 16; ++v) {
+    const int len = S.padfrom[v];
+    for (int j = 0, st = 0; j < len; ++j)
+      if (S.words[(size_t)j * 16 + v] & kSlotEnd) {
+        rstart[v].push_back(st);
+        rlen[v].push_back(j + 1 - st);
+        st = j + 1;
+      }
+    const int R = (int)rlen[v].size();
+    int best = len;
+    unsigned bestm = 0u;
+    if (R <= 16) {
+      for (unsigned msk = 0; msk < (1u << R); ++msk) {
+        int l1 = 0;
+        for (int r = 0; r < R; ++r)
+          if ((msk >> r) & 1u) l1 += rlen[v][r];
+        const int m = std::max(l1, len - l1);
+        if (m < best) {
+          best = m;
+          bestm = msk;
+        }
+      }
+    } else {
+      std::vector<int> ord(R);
+      for (int r = 0; r < R; ++r) ord[r] = r;
+      std::stable_sort(ord.begin(), ord.end(),
+                       [&](int x, int y) { return rlen[v][x] > rlen[v][y]; });
+      int l0 = 0, l1 = 0;
+      for (int r : ord) {
+        if (l1 < l0) {
+          l1 += rlen[v][r];
+          bestm |= 1u << (r & 31);  // (R > 16 does not occur at 5 rows per lane)
+        } else {
+          l0 += rlen[v][r];
+        }
+      }
+      best = std::max(l0, l1);
+    }
+    side[v] = bestm;
+    L2 = std::max(L2, best);
+  }
+  S.L2 = L2;
+  S.words2.assign((size_t)L2 * 32, 0u);
+  S.padfrom2.assign(32, 0);
+  S.dst2.assign(nnz, -1);
+  S.dslot2.assign(n, -1);
+  std::vector<int> map16((size_t)S.L * 16, -1);
+  for (int v = 0; v < 16; ++v) {
+    int fill[2] = {0, 0};
+    for (size_t r = 0; r < rlen[v].size(); ++r) {
+      const int h = (side[v] >> r) & 1u;
+      const int lane = v + 16 * h;
+      for (int q = 0; q < rlen[v][r]; ++q) {
+        const size_t t16 = (size_t)(rstart[v][r] + q) * 16 + v;
+        const size_t t2 = (size_t)fill[h]++ * 32 + lane;
+        S.words2[t2] = S.words[t16];
+        map16[t16] = (int)t2;
+        if (S.src[t16] >= 0) S.dst2[S.src[t16]] = (int)t2;
+      }
+    }
+    S.padfrom2[v] = fill[0];
+    S.padfrom2[v + 16] = fill[1];
+  }
+  for (int r = 0; r < n; ++r)
+    if (S.dslot[r] >= 0) S.dslot2[r] = map16[S.dslot[r]];
+}
 
 Schedule build_schedule(int n, const std::vector<int> &rp,
                         const std::vector<int> &ci, const std::vector<int> &perm,
@@ -335,6 +422,9 @@ struct camp_solver {
   // switch that treats every cooperative launch as refused
   long long ord_wait = kOrdWaitCycles;
   int refuse_cooperative = 0;
+  // single-cell tickets of the plain 16-lane launch: < 0 automatic, else the
+  // number of tail pairs solved as single cells (camp_solver_set_single_tail)
+  int single_tail = -1;
 };
 
 namespace {
@@ -343,17 +433,26 @@ cudaError_t view_schedule(View &v, int Lc, Schedule **out) {
   auto it = v.sched.find(Lc);
   if (it == v.sched.end()) {
     Schedule S = build_schedule(v.n, v.rp, v.ci, v.perm, v.diag, Lc);
+    split_schedule(S, v.n, v.nnz);
     cudaError_t e = upload(&S.d_words, S.words);
     if (e == cudaSuccess) e = upload(&S.d_src, S.src);
     if (e == cudaSuccess) e = upload(&S.d_dslot, S.dslot);
     if (e == cudaSuccess) e = upload(&S.d_dst, S.dst);
     if (e == cudaSuccess) e = upload(&S.d_padfrom, S.padfrom);
+    if (e == cudaSuccess && S.L2) e = upload(&S.d_words2, S.words2);
+    if (e == cudaSuccess && S.L2) e = upload(&S.d_dst2, S.dst2);
+    if (e == cudaSuccess && S.L2) e = upload(&S.d_padfrom2, S.padfrom2);
+    if (e == cudaSuccess && S.L2) e = upload(&S.d_dslot2, S.dslot2);
     if (e != cudaSuccess) {
       cudaFree(S.d_words);
       cudaFree(S.d_src);
       cudaFree(S.d_dslot);
       cudaFree(S.d_dst);
       cudaFree(S.d_padfrom);
+      cudaFree(S.d_words2);
+      cudaFree(S.d_dst2);
+      cudaFree(S.d_padfrom2);
+      cudaFree(S.d_dslot2);
       return e;
     }
     it = v.sched.emplace(Lc, std::move(S)).first;
@@ -373,6 +472,10 @@ void free_view(View &v) {
     cudaFree(kv.second.d_dslot);
     cudaFree(kv.second.d_dst);
     cudaFree(kv.second.d_padfrom);
+    cudaFree(kv.second.d_words2);
+    cudaFree(kv.second.d_dst2);
+    cudaFree(kv.second.d_padfrom2);
+    cudaFree(kv.second.d_dslot2);
   }
   v.sched.clear();
 }
@@ -709,6 +812,44 @@ cudaError_t launch_cooperative(camp_solver_t h, bool cooperative, Launch launch)
   return launch();
 }
 
+// Single-cell tickets of a plain launch at 16 lanes per cell (warp_single.cuh):
+// the last R pairs of the launch become 2R single-cell tickets.  Automatic R
+// (measured at 80 species on 152 SMs x 16 warps): every pair when the pairs
+// would keep at most a quarter of the resident warps busy (a lone warp's
+// latency decides such a launch: 60 against 75 us at 64 to 608 cells, 65.5
+// against 75.8 at 1,212), else none (at full load one cell per warp costs
+// about 13 % more per cell, and turning the pairs past the last full wave
+// into singles measured within the noise at 10,000 cells).
+// camp_solver_set_single_tail overrides it.  Sets
+// single_from, ngroups (tickets) and the split schedule's arguments; leaves
+// the launch without single tickets when the split schedule does not fit
+// the warp's region.
+void set_single_tickets(camp_solver_t h, const Schedule &S, WarpArgs &a, int wpb, int occ) {
+  const int pairs = a.ngroups;
+  a.single_from = pairs;
+  a.sched2 = nullptr;
+  if (S.L2 == 0 || a.Lc != 16 || a.k != 2 || h->single_tail == 0) return;
+  const int E16 = (a.n + 15) / 16;
+  const size_t need = ((size_t)(S.L2 * 32 + 1) & ~(size_t)1) + 3 * (size_t)(((16 * E16 + 1) + 1) & ~1);
+  if (E16 > kRegVecMaxE || need > 2 * (size_t)a.segStride) return;
+  const long resident = (long)h->sms * occ * wpb;  // warps the GPU holds at once
+  int R = 0;
+  if (h->single_tail > 0) {
+    R = std::min(pairs, h->single_tail);
+  } else if (4L * pairs <= resident) {
+    R = pairs;  // a small batch: every cell alone, each warp nearly so
+  }
+  if (R == 0) return;
+  const int P = pairs - R;
+  a.single_from = P;
+  a.ngroups = P + std::max(0, a.cells - 2 * P);
+  a.L2 = S.L2;
+  a.sched2 = S.d_words2;
+  a.dst2 = S.d_dst2;
+  a.padfrom2 = S.d_padfrom2;
+  a.dslot2 = S.d_dslot2;
+}
+
 camp_status do_solve(camp_solver_t h, int cells, const double *A_vals,
                      const double *b, double *x, double tol, int maxit,
                      int *iters_out, double *resid_out, int *status_out,
@@ -772,6 +913,7 @@ camp_status do_solve(camp_solver_t h, int cells, const double *A_vals,
     e = warp_occupancy(E, wpb, smem, &occ);
     if (e != cudaSuccess) return cuda_fail(e, "occupancy");
     if (occ < 1) occ = 1;
+    set_single_tickets(h, *S, a, wpb, occ);
     if (queue_slot == 0) {
       const camp_status rs = setup_ordering(h, a, A_vals, smem - sched_smem_bytes(S->L * Lc), st,
                                             &calibrate);
@@ -817,7 +959,7 @@ camp_status do_solve(camp_solver_t h, int cells, const double *A_vals,
 extern "C" {
 
 const char *camp_last_error(void) { return g_err.c_str(); }
-const char *camp_version(void) { return "campsolve 0.15 (sm_103a)"; }
+const char *camp_version(void) { return "campsolve 0.16 (sm_103a)"; }
 
 camp_status camp_schedule_build(int n, int nnz, const int *row_ptr,
                                 const int *col_idx, int lanes_per_cell,
@@ -852,6 +994,43 @@ camp_status camp_schedule_build(int n, int nnz, const int *row_ptr,
     for (size_t q = 0; q < S.words.size(); ++q) {
       words[2 * q] = (unsigned)S.src[q];
       words[2 * q + 1] = S.words[q];
+    }
+  }
+  return CAMP_OK;
+}
+
+camp_status camp_schedule_build_split(int n, int nnz, const int *row_ptr,
+                                      const int *col_idx, unsigned *words,
+                                      int capacity_slots, int *slots_per_lane) {
+  if (!row_ptr || !col_idx || !slots_per_lane) return fail(CAMP_EINVAL, "null argument");
+  if (n < 1 || n > 1024 || nnz < n || nnz > 65535 || row_ptr[n] != nnz)
+    return fail(CAMP_EINVAL, "bad sizes");
+  if ((n + 15) / 16 > 5) return fail(CAMP_EUNSUPPORTED, "more than 5 rows per lane at 16 lanes");
+  if (row_ptr[0] != 0) return fail(CAMP_EPATTERN, "row_ptr[0] must be 0");
+  for (int i = 0; i < n; ++i)
+    if (row_ptr[i + 1] < row_ptr[i] || row_ptr[i + 1] > nnz)
+      return fail(CAMP_EPATTERN, "row_ptr not nondecreasing within [0, nnz] at row %d", i);
+  std::vector<int> rp(row_ptr, row_ptr + n + 1), ci(col_idx, col_idx + nnz), diag(n, -1);
+  for (int i = 0; i < n; ++i) {
+    for (int k = rp[i]; k < rp[i + 1]; ++k) {
+      if (ci[k] < 0 || ci[k] >= n)
+        return fail(CAMP_EPATTERN, "column %d out of range at entry %d", ci[k], k);
+      if (ci[k] == i) diag[i] = k;
+    }
+    if (diag[i] < 0) return fail(CAMP_EPATTERN, "diagonal entry missing in row %d", i);
+  }
+  Schedule S = build_schedule(n, rp, ci, std::vector<int>(), diag, 16);
+  split_schedule(S, n, nnz);
+  *slots_per_lane = S.L2;
+  if (words) {
+    if ((long)S.L2 * 32 > (long)capacity_slots)
+      return fail(CAMP_EINVAL, "capacity %d < %d slots", capacity_slots, S.L2 * 32);
+    std::vector<unsigned> entry((size_t)S.L2 * 32, 0xFFFFFFFFu);
+    for (int k = 0; k < nnz; ++k)
+      if (S.dst2[k] >= 0) entry[S.dst2[k]] = (unsigned)k;
+    for (size_t q = 0; q < S.words2.size(); ++q) {
+      words[2 * q] = entry[q];
+      words[2 * q + 1] = S.words2[q];
     }
   }
   return CAMP_OK;
@@ -1016,6 +1195,13 @@ camp_status camp_solver_get_fault(camp_solver_t h, int *ordering_timed_out) {
     *ordering_timed_out = 1;
     *(volatile int *)h->h_ord_err = 0;
   }
+  return CAMP_OK;
+}
+
+camp_status camp_solver_set_single_tail(camp_solver_t h, int pairs) {
+  if (!h) return fail(CAMP_EINVAL, "null solver handle");
+  std::lock_guard<std::mutex> lock(h->mu);
+  h->single_tail = pairs < 0 ? -1 : pairs;
   return CAMP_OK;
 }
 

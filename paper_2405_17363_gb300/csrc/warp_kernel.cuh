@@ -24,6 +24,7 @@
 #pragma once
 #include <type_traits>
 #include "warp_common.cuh"
+#include "warp_single.cuh"
 
 namespace camp {
 
@@ -559,6 +560,18 @@ __device__ __forceinline__ void plain_launch_body(const WarpArgs &a) {
         if (g >= (unsigned)a.ngroups) break;
         if (a.order && a.ord_stride && g < (unsigned)a.ord_wave)
           g = (unsigned)((unsigned long long)g * (unsigned)a.ord_stride % (unsigned)a.ord_wave);
+      }
+      if constexpr (SRC == kSrcStaged && LC == 16 && E <= kRegVecMaxE) {
+        if (a.sched2 && (int)g >= a.single_from) {
+          // a single-cell ticket: one cell on all 32 lanes (warp_single.cuh)
+          const int ps = 2 * a.single_from + ((int)g - a.single_from);
+          const bool one = a.ord_ws && lane == 0 && ps < a.cells;
+          if (one) wait_order_entry(a.order + ps, a.ord_ws + kOrdFlag, a.ord_err, a.ord_wait);
+          __syncwarp();
+          solve_single<E>(a, ps, wbase);
+          if (one) a.ord_out[ps] = 0;
+          continue;
+        }
       }
       // in-launch ordering: wait for this group's order entries, solve,
       // then clear them

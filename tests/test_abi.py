@@ -270,3 +270,82 @@ def test_schedule_build_rejects_columns_out_of_range(lib):
         assert "out of range" in _msg(lib)
     ci = np.array([0, 2, 0, 1, 2], np.int32)
     assert f(3, 5, rp.ctypes.data, ci.ctypes.data, 1, None, 0, ctypes.byref(L)) == 0
+
+
+def _rows_of_schedule(w, L, lanes):
+    """Per row, the sequence of entries its sum multiplies, in slot order."""
+    rows = {}
+    for lane in range(lanes):
+        cur = []
+        for j in range(L):
+            src, w1 = int(w[j, lane, 0]), int(w[j, lane, 1])
+            if src == 0xFFFFFFFF:
+                assert not w1 >> 31
+                continue
+            cur.append(src)
+            if w1 >> 31:
+                row = (w1 >> 11) & 0x7FF
+                assert row not in rows
+                rows[row] = cur
+                cur = []
+        assert not cur, "entries after a lane's last row end"
+    return rows
+
+
+@pytest.mark.parametrize("wid", [0, 1, 2, 5])
+def test_split_schedule_keeps_every_row_chain(lib, wid):
+    """The split schedule behind single-cell tickets (one cell on 32 lanes)
+    gives every row exactly the entries, in exactly the order, of the 16-lane
+    schedule (so each row's sum is the same chain of multiply-adds), lane
+    v + 16 takes only rows of 16-lane lane v, and the split halves the slots
+    per lane to within the longest row."""
+    import synth
+    cbs, _, _ = synth.workload(wid, cells=1)
+    for cb in cbs:
+        m = cb.mech
+        if (m.n + 15) // 16 > 5:
+            continue
+        L16, w16 = _schedule(lib, "camp_schedule_build", m, 16)
+        f = lib.camp_schedule_build_split
+        f.restype = ctypes.c_int
+        f.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
+                      ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]
+        rp = np.ascontiguousarray(m.row_ptr, np.int32)
+        ci = np.ascontiguousarray(m.col_idx, np.int32)
+        L = ctypes.c_int()
+        assert f(m.n, m.nnz, rp.ctypes.data, ci.ctypes.data, None, 0, ctypes.byref(L)) == 0
+        words = np.zeros(2 * L.value * 32, np.uint32)
+        assert f(m.n, m.nnz, rp.ctypes.data, ci.ctypes.data, words.ctypes.data, L.value * 32,
+                 ctypes.byref(L)) == 0
+        w2 = words.reshape(L.value, 32, 2)
+        r16 = _rows_of_schedule(w16, L16, 16)
+        r2 = _rows_of_schedule(w2, L.value, 32)
+        assert r16 == r2
+        assert set(r16) == set(range(m.n))
+        # lane v + 16 holds rows of 16-lane lane v
+        lane16 = {}
+        for lane in range(16):
+            for j in range(L16):
+                if w16[j, lane, 0] != 0xFFFFFFFF:
+                    lane16[(int(w16[j, lane, 1]) >> 11) & 0x7FF] = lane
+        for lane in range(32):
+            for j in range(L.value):
+                if w2[j, lane, 0] != 0xFFFFFFFF:
+                    assert lane16[(int(w2[j, lane, 1]) >> 11) & 0x7FF] == lane % 16
+        longest = int(np.diff(m.row_ptr).max())
+        assert L.value <= (L16 + 1) // 2 + longest, (L.value, L16, longest)
+
+
+def _schedule(lib, fn, m, lc):
+    f = getattr(lib, fn)
+    f.restype = ctypes.c_int
+    f.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
+                  ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]
+    rp = np.ascontiguousarray(m.row_ptr, np.int32)
+    ci = np.ascontiguousarray(m.col_idx, np.int32)
+    L = ctypes.c_int()
+    assert f(m.n, m.nnz, rp.ctypes.data, ci.ctypes.data, lc, None, 0, ctypes.byref(L)) == 0
+    words = np.zeros(2 * max(1, L.value * lc), np.uint32)
+    assert f(m.n, m.nnz, rp.ctypes.data, ci.ctypes.data, lc, words.ctypes.data,
+             L.value * lc, ctypes.byref(L)) == 0
+    return L.value, words[:2 * L.value * lc].reshape(L.value, lc, 2)
