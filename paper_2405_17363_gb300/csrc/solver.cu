@@ -142,7 +142,7 @@ CAMP_OCCUPANCY8(newton_occupancy, newton)
 #undef CAMP_DISPATCH8
 #undef CAMP_OCCUPANCY8
 
-constexpr int kHostChunks = 6;        // pipeline depth of camp_solver_solve_host
+constexpr int kHostChunks = 5;        // pipeline depth of camp_solver_solve_host
 constexpr int kHostSolveStreams = 4;  // concurrent chunk solves
 
 cudaError_t ensure_max_smem(const void *kernel) {
