@@ -1,6 +1,7 @@
 // Host layer of the C ABI (include/camp_solver.h): pattern validation and
 // preprocessing, SpMV schedules, arrangement choice and kernel launches.
 #include <algorithm>
+#include <cstdint>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -1313,11 +1314,25 @@ camp_status camp_solver_solve_host(camp_solver_t h, int cells,
     c0s[nchunk] = cells;
   }
   cudaMemcpyAsync(h->h_db, b, (size_t)cells * n * 8, cudaMemcpyHostToDevice, sin);
-  for (int q = 0; q < nchunk; ++q) {
-    const int c0 = c0s[q], cn = c0s[q + 1] - c0;
-    cudaMemcpyAsync(h->h_dA + (size_t)c0 * nnz, A_vals + (size_t)c0 * nnz,
-                    (size_t)cn * nnz * 8, cudaMemcpyHostToDevice, sin);
-    cudaEventRecord(h->h_in[q], sin);
+  // each copy ends at the first 4 KiB boundary of the source at or past its
+  // chunk's last cell (a copy that starts inside a page ran 10-20 us slower
+  // per boundary); a chunk's solve waits for the copy that holds its last byte
+  {
+    const size_t totA = (size_t)cells * nnz * 8;
+    const uintptr_t base = reinterpret_cast<uintptr_t>(A_vals);
+    size_t from = 0;
+    for (int q = 0; q < nchunk; ++q) {
+      const size_t want = (size_t)c0s[q + 1] * nnz * 8;
+      const size_t to = q + 1 == nchunk
+                            ? totA
+                            : std::min(totA, (size_t)(((base + want + 4095) & ~(uintptr_t)4095) - base));
+      if (to > from)
+        cudaMemcpyAsync(reinterpret_cast<char *>(h->h_dA) + from,
+                        reinterpret_cast<const char *>(A_vals) + from, to - from,
+                        cudaMemcpyHostToDevice, sin);
+      cudaEventRecord(h->h_in[q], sin);
+      from = std::max(from, to);
+    }
   }
   for (int q = 1; q < 2 + kHostSolveStreams; ++q) cudaStreamWaitEvent(h->h_streams[q], h->h_start, 0);
   // Outputs in host memory the device can address (pinned or mapped) are
