@@ -349,3 +349,31 @@ def _schedule(lib, fn, m, lc):
     assert f(m.n, m.nnz, rp.ctypes.data, ci.ctypes.data, lc, words.ctypes.data,
              L.value * lc, ctypes.byref(L)) == 0
     return L.value, words[:2 * L.value * lc].reshape(L.value, lc, 2)
+
+
+def test_single_tail_and_split_export_validate_without_gpu(lib):
+    """camp_solver_set_single_tail rejects a null handle; the split-schedule
+    export rejects patterns its 16-lane layout cannot take (more than 5 rows
+    per lane: EUNSUPPORTED) and bad patterns (EPATTERN), before any work."""
+    EINVAL, EPATTERN, EUNSUPPORTED = -1, -4, -5
+    f = lib.camp_solver_set_single_tail
+    f.restype = ctypes.c_int
+    f.argtypes = [ctypes.c_void_p, ctypes.c_int]
+    assert f(None, 3) == EINVAL
+    g = lib.camp_schedule_build_split
+    g.restype = ctypes.c_int
+    g.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                  ctypes.c_int, ctypes.POINTER(ctypes.c_int)]
+    L = ctypes.c_int()
+    n = 81  # 6 rows per lane at 16 lanes
+    rp = np.arange(n + 1, dtype=np.int32)
+    ci = np.arange(n, dtype=np.int32)
+    assert g(n, n, rp.ctypes.data, ci.ctypes.data, None, 0, ctypes.byref(L)) == EUNSUPPORTED
+    n = 40
+    rp = np.arange(n + 1, dtype=np.int32)
+    ci = np.arange(n, dtype=np.int32)
+    ci[7] = 8  # row 7 without its diagonal entry
+    assert g(n, n, rp.ctypes.data, ci.ctypes.data, None, 0, ctypes.byref(L)) == EPATTERN
+    ci[7] = 7
+    assert g(n, n, rp.ctypes.data, ci.ctypes.data, None, 0, ctypes.byref(L)) == 0
+    assert L.value >= 1
