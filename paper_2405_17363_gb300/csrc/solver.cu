@@ -228,7 +228,7 @@ struct Schedule {
 void split_schedule(Schedule &S, int n, int nnz) {
   if (S.Lc != 16 || S.L == 0) return;
   std::vector<std::vector<int>> rstart(16), rlen(16);
-  std::vector<unsigned> side(16, 0u);  // bit r: row r of the lane goes to lane v + 16
+  std::vector<std::vector<char>> side(16);  // side[v][r]: row r of lane v goes to lane v + 16
   int L2 = 1;
   for (int v = 0; v < 16; ++v) {
     const int len = S.padfrom[v];
@@ -239,9 +239,10 @@ void split_schedule(Schedule &S, int n, int nnz) {
         st = j + 1;
       }
     const int R = (int)rlen[v].size();
+    side[v].assign(R, 0);
     int best = len;
-    unsigned bestm = 0u;
     if (R <= 16) {
+      unsigned bestm = 0u;
       for (unsigned msk = 0; msk < (1u << R); ++msk) {
         int l1 = 0;
         for (int r = 0; r < R; ++r)
@@ -252,6 +253,7 @@ void split_schedule(Schedule &S, int n, int nnz) {
           bestm = msk;
         }
       }
+      for (int r = 0; r < R; ++r) side[v][r] = (char)((bestm >> r) & 1u);
     } else {
       std::vector<int> ord(R);
       for (int r = 0; r < R; ++r) ord[r] = r;
@@ -261,14 +263,13 @@ void split_schedule(Schedule &S, int n, int nnz) {
       for (int r : ord) {
         if (l1 < l0) {
           l1 += rlen[v][r];
-          bestm |= 1u << (r & 31);  // (R > 16 does not occur at 5 rows per lane)
+          side[v][r] = 1;
         } else {
           l0 += rlen[v][r];
         }
       }
       best = std::max(l0, l1);
     }
-    side[v] = bestm;
     L2 = std::max(L2, best);
   }
   S.L2 = L2;
@@ -280,7 +281,7 @@ void split_schedule(Schedule &S, int n, int nnz) {
   for (int v = 0; v < 16; ++v) {
     int fill[2] = {0, 0};
     for (size_t r = 0; r < rlen[v].size(); ++r) {
-      const int h = (side[v] >> r) & 1u;
+      const int h = side[v][r];
       const int lane = v + 16 * h;
       for (int q = 0; q < rlen[v][r]; ++q) {
         const size_t t16 = (size_t)(rstart[v][r] + q) * 16 + v;

@@ -377,3 +377,31 @@ def test_single_tail_and_split_export_validate_without_gpu(lib):
     ci[7] = 7
     assert g(n, n, rp.ctypes.data, ci.ctypes.data, None, 0, ctypes.byref(L)) == 0
     assert L.value >= 1
+
+
+def test_split_schedule_with_many_rows_on_one_lane(lib):
+    """A pattern whose 16-lane schedule puts more than 32 rows on one lane
+    (15 long rows fill 15 lanes, 65 diagonal-only rows go to the 16th): the
+    split (greedy past 16 rows per lane) still keeps every row's chain."""
+    import synth
+    n = 80
+    rows = [sorted(set(range(0, 60)) | {i}) for i in range(15)] + [[i] for i in range(15, n)]
+    rp = np.r_[0, np.cumsum([len(r) for r in rows])].astype(np.int32)
+    ci = np.concatenate([np.array(r, np.int32) for r in rows])
+    m = synth.Mechanism(n=n, R=0, reactants=None, products=None, k=None, row_ptr=rp, col_idx=ci)
+    L16, w16 = _schedule(lib, "camp_schedule_build", m, 16)
+    lanes_rows = [sum(1 for j in range(L16) if w16[j, q, 0] != 0xFFFFFFFF and w16[j, q, 1] >> 31)
+                  for q in range(16)]
+    assert max(lanes_rows) > 32
+    f = lib.camp_schedule_build_split
+    f.restype = ctypes.c_int
+    f.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
+                  ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]
+    L = ctypes.c_int()
+    assert f(n, m.nnz, rp.ctypes.data, ci.ctypes.data, None, 0, ctypes.byref(L)) == 0
+    words = np.zeros(2 * L.value * 32, np.uint32)
+    assert f(n, m.nnz, rp.ctypes.data, ci.ctypes.data, words.ctypes.data, L.value * 32,
+             ctypes.byref(L)) == 0
+    w2 = words.reshape(L.value, 32, 2)
+    assert _rows_of_schedule(w16, L16, 16) == _rows_of_schedule(w2, L.value, 32)
+    assert L.value <= L16
