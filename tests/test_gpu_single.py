@@ -104,3 +104,25 @@ def test_single_tickets_edge_cases(cuda):
     _assert_same(ref, got, "edge cases")
     assert int(got[3][2]) == camp.CAMP_CELL_NONFINITE and int(got[1][1]) == 0
     s.close()
+
+
+@pytest.mark.parametrize("n,R", [(12, 20), (24, 48), (40, 90), (56, 130), (80, 200)])
+def test_single_tickets_every_rows_per_lane(cuda, n, R):
+    """At 16 lanes per cell with 1 to 5 rows per lane (the split gives the
+    upper lanes 0, 1, 1, 2 and 2 rows; odd counts leave them a spare slot):
+    single tickets bit for bit the pair solve, on 1,001 cells."""
+    import torch
+    from paper_2405_17363_gb300 import camp
+    m = synth.make_mechanism(n, R, 500 + n)
+    cb = synth.make_cells(m, 1001, 600 + n, gamma=(1e-4, 1e-1))
+    A = torch.as_tensor(cb.A_vals, device=cuda)
+    b = torch.as_tensor(cb.b, device=cuda)
+    s = camp.Solver(m.row_ptr, m.col_idx)
+    s.set_arrangement(camp.CAMP_ARR_WARP, 16, 1, 0)
+    ref = _solve(camp, s, A, b, 1e-10, 500, 0, 0)
+    for tail in (77, ALL):
+        for ordering in (0, 1):
+            got = _solve(camp, s, A, b, 1e-10, 500, tail, ordering)
+            _assert_same(ref, got, f"n {n} tail {tail} ordering {ordering}")
+    assert int((ref[3] == 0).sum()) == 1001
+    s.close()
