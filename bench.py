@@ -436,6 +436,31 @@ def time_cfg4(camp, dev, flush, stream, steps=10, threads=None):
     return res
 
 
+def time_small_batches(camp, cb, tol, maxit, flush, stream, dev, steps=200):
+    """Small batches of the headline cells (64 and 608 cells, where one pair
+    per warp would keep at most a quarter of the GPU's warps busy): the
+    library's automatic launch, which solves each cell alone on a warp
+    (single-cell tickets, bit for bit the pair solve), against the same
+    launch with pairs only.  Median microseconds per solve, L2 flushed."""
+    import torch
+    m = cb.mech
+    s = camp.Solver(m.row_ptr, m.col_idx)
+    out = {}
+    for C in (64, 608):
+        A = torch.as_tensor(cb.A_vals[:C], device=dev)
+        b = torch.as_tensor(cb.b[:C], device=dev)
+        row = {"cells": C}
+        for name, tail in (("automatic_us", -1), ("pairs_only_us", 0)):
+            s.set_single_tail(tail)
+            res = s.solve(A, b, tol, maxit)
+            t = time_steps(lambda: s.solve(A, b, tol, maxit, out=res), flush, stream, steps, 5)
+            row[name] = float(np.median(t)) * 1000.0
+        s.set_single_tail(-1)
+        out[str(C)] = row
+    s.close()
+    return out
+
+
 def time_adjoint(camp, dev, flush, stream, steps=50):
     """The adjoint workload (80 species / 200 reactions, 10,000 cells): one
     forward solve and the backward of L = sum_c w_c . x_c as the library's
@@ -786,7 +811,7 @@ def main():
 
     mixed_side = None
     e2e = None
-    uneven = var_rows = cfg4 = adjoint = None
+    uneven = var_rows = cfg4 = adjoint = small = None
     fused = None
     newton = None
     fp64_measured = None
@@ -811,6 +836,7 @@ def main():
             var_rows = variability(camp, dev, flush, stream, 20)
             cfg4 = time_cfg4(camp, dev, flush, stream)
             adjoint = time_adjoint(camp, dev, flush, stream)
+            small = time_small_batches(camp, cb, tol, maxit, flush, stream, dev)
 
     if rank == 0:
         cpu = cpu_baseline(m, cb.A_vals, cb.b, tol, maxit, args.cpu_seconds) \
@@ -860,6 +886,8 @@ def main():
             line["mixed_cfg4"] = cfg4
         if adjoint is not None:
             line["adjoint"] = adjoint
+        if small is not None:
+            line["small_batches"] = small
         if fused is not None:
             line["fused_assembly"] = fused
         if newton is not None:
