@@ -961,7 +961,7 @@ camp_status do_solve(camp_solver_t h, int cells, const double *A_vals,
 extern "C" {
 
 const char *camp_last_error(void) { return g_err.c_str(); }
-const char *camp_version(void) { return "campsolve 0.16 (sm_103a)"; }
+const char *camp_version(void) { return "campsolve 0.17 (sm_103a)"; }
 
 camp_status camp_schedule_build(int n, int nnz, const int *row_ptr,
                                 const int *col_idx, int lanes_per_cell,

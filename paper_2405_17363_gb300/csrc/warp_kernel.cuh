@@ -325,14 +325,20 @@ __device__ __forceinline__ void solve_group(const WarpArgs &a, int g,
   }
 
   bool restart = !done, first = true;
+  bool pass0 = true;  // the solve's first (re)start, the same for every segment
   bool fin = false, active = false, broke = false, nonfin = false;
   double rho = 1.0, rho_prev = 1.0, alpha = 1.0, omega = 1.0;
   for (;;) {
     {  // (re)start from the current residual r
       double acc[1] = {0.0};
+      if (pass0 && !a.x0_given) {
+        acc[0] = bb;  // r = b: the same chain and exact sum as ||b||^2
+      } else {
 #pragma unroll
-      for (int e = 0; e < E; ++e) acc[0] = fma(r[e], r[e], acc[0]);
-      acc[0] = ssum1<LC>(acc[0], Lc);
+        for (int e = 0; e < E; ++e) acc[0] = fma(r[e], r[e], acc[0]);
+        acc[0] = ssum1<LC>(acc[0], Lc);
+      }
+      pass0 = false;
       if (restart) {
 #pragma unroll
         for (int e = 0; e < E; ++e) {

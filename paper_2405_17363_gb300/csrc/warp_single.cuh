@@ -134,13 +134,19 @@ __device__ __forceinline__ void solve_single(const WarpArgs &a, int pos, double 
   }
 
   bool restart = !done, first = true;
+  bool pass0 = true;  // the solve's first (re)start
   bool fin = false, active = false, broke = false, nonfin = false;
   double rho = 1.0, rho_prev = 1.0, alpha = 1.0, omega = 1.0;
   for (;;) {
     {  // (re)start from the current residual r
       double acc = 0.0;
-      CHAIN(acc, r[j], r[j]);
-      acc = seg_sum_exact_redux<1>(acc);
+      if (pass0 && !a.x0_given) {
+        acc = bb;  // r = b: the same chain and exact sum as ||b||^2
+      } else {
+        CHAIN(acc, r[j], r[j]);
+        acc = seg_sum_exact_redux<1>(acc);
+      }
+      pass0 = false;
       if (restart) {
 #pragma unroll
         for (int j = 0; j < E0; ++j) {
