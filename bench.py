@@ -436,17 +436,17 @@ def time_cfg4(camp, dev, flush, stream, steps=10, threads=None):
     return res
 
 
-def time_small_batches(camp, cb, tol, maxit, flush, stream, dev, steps=200):
-    """Small batches of the headline cells (64 and 608 cells, where one pair
-    per warp would keep at most a quarter of the GPU's warps busy): the
-    library's automatic launch, which solves each cell alone on a warp
+def time_small_batches(camp, cb, tol, maxit, flush, stream, dev, steps=200, sizes=(64, 608)):
+    """Small batches of the headline cells (by default 64 and 608 cells, where
+    one pair per warp would keep at most a quarter of the GPU's warps busy):
+    the library's automatic launch, which solves each cell alone on a warp
     (single-cell tickets, bit for bit the pair solve), against the same
     launch with pairs only.  Median microseconds per solve, L2 flushed."""
     import torch
     m = cb.mech
     s = camp.Solver(m.row_ptr, m.col_idx)
     out = {}
-    for C in (64, 608):
+    for C in sizes:
         A = torch.as_tensor(cb.A_vals[:C], device=dev)
         b = torch.as_tensor(cb.b[:C], device=dev)
         row = {"cells": C}
@@ -628,6 +628,23 @@ def run_side_case(args):
     print(json.dumps({"case": args.case, **res}), flush=True)
 
 
+def run_small_case(args):
+    """--case small: the small-batch block alone (automatic launch against
+    pairs only) at the sizes --cells lists, e.g. for profiling a lone warp."""
+    import torch
+    from paper_2405_17363_gb300 import camp
+    dev = torch.device("cuda", 0)
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+    cbs, tol, maxit = synth.workload(WORKLOAD_ID)
+    sizes = tuple(int(c) for c in args.cells.split(","))
+    if not sizes or min(sizes) < 1 or max(sizes) > cbs[0].cells:
+        raise SystemExit(f"--cells must list sizes in [1, {cbs[0].cells}]")
+    res = time_small_batches(camp, cbs[0], tol, maxit, flush, torch.cuda.current_stream(), dev,
+                             steps=args.steps, sizes=sizes)
+    print(json.dumps({"case": "small", "workload": synth.WORKLOADS[WORKLOAD_ID][0],
+                      "unit": "us per solve", "sizes": res}), flush=True)
+
+
 def run_uneven_case(args):
     """--case uneven: the persistent batch alone, timed as the step."""
     import torch
@@ -718,11 +735,14 @@ def main():
                     help="fp64: plain FP64 solve (the headline); mixed: FP32-inner refinement")
     ap.add_argument("--case", default="headline",
                     choices=["headline", "uneven", "arrangements", "variability", "fused",
-                             "newton", "cfg4", "adjoint"],
+                             "newton", "cfg4", "adjoint", "small"],
                     help="headline: the 80-species 10k-cell FP64 solve; uneven: time the "
                          "persistent multi-mechanism batch as the step; fused / newton: the "
                          "in-kernel assembly or the device Newton corrector alone (for "
-                         "profiling)")
+                         "profiling); small: small batches (--cells) automatic against pairs "
+                         "only")
+    ap.add_argument("--cells", default="64,608",
+                    help="--case small: comma-separated batch sizes of headline cells")
     ap.add_argument("--ordering", type=int, default=None, choices=[0, 1, 2],
                     help="cell ordering: 0 index order, 1 hardest first ordered inside the "
                          "solve launch, 2 hardest first by a separate pass (default: the "
@@ -752,6 +772,8 @@ def main():
         return run_step_case(args)
     if args.case in ("cfg4", "adjoint"):
         return run_side_case(args)
+    if args.case == "small":
+        return run_small_case(args)
 
     import torch
     import torch.distributed as dist
